@@ -1,0 +1,183 @@
+"""Pins for the oracle's FP64 ADMM, quantizer, decode and private loop
+(oracle/admm.py).
+
+Ties: soft-threshold closed form; the LASSO closed form S_lambda(A^T y) for an
+orthonormal design; the KKT conditions of the LASSO at convergence (global for
+the centralised ADMM, per block for the distributed one, whose fixed point
+solves each node's own LASSO); K = 1 reduces to the centralised ADMM; the
+quantizers against their definition; the decode against exact rational
+arithmetic; Theorem 1 (real encryption gives the same decrypted integers and
+iterates as the plain-integer evaluation); and the quantization error bound."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import admm as O
+from oracle import paillier as P
+from paper_2601_14980_b300 import workloads as W
+
+
+def test_soft_threshold_closed_form():
+    a = np.array([-3.0, -1.0, -0.5, 0.0, 0.5, 1.0, 1.0000001, 3.0])
+    k = 1.0
+    expect = np.array([-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0000001 - 1.0, 2.0])
+    assert np.array_equal(O.soft_threshold(a, k), expect)
+
+
+def test_cen_admm_orthonormal_design_closed_form():
+    rng = np.random.default_rng(0)
+    M, N = 60, 40
+    A, _ = np.linalg.qr(rng.standard_normal((M, N)))   # A^T A = I
+    y = rng.standard_normal(M)
+    lam, rho = 0.3, 1.0
+    x, z, v = O.cen_admm(A, y, lam, rho, 400)
+    xstar = O.soft_threshold(A.T @ y, lam)
+    assert np.allclose(z, xstar, atol=1e-10)
+
+
+def _kkt_gap(A, y, x, lam):
+    g = A.T @ (y - A @ x)
+    nz = np.abs(x) > 1e-9
+    gap_nz = np.max(np.abs(g[nz] - lam * np.sign(x[nz]))) if nz.any() else 0.0
+    gap_z = np.max(np.abs(g[~nz]) - lam) if (~nz).any() else -1.0
+    return gap_nz, gap_z
+
+
+def test_cen_admm_kkt():
+    L = W.lasso_small(seed=5, M=40, N=80, nnz=6)
+    x, z, v = O.cen_admm(L.A, L.y, 0.05, 1.0, 3000)
+    gnz, gz = _kkt_gap(L.A, L.y, z, 0.05)
+    assert gnz < 1e-6 and gz < 1e-6
+
+
+def test_dis_admm_blockwise_kkt_and_k1():
+    L = W.lasso_small(seed=6, M=40, N=80, nnz=6)
+    sizes = W.node_sizes(80, 4)
+    st = O.dis_setup(L.A, L.y, sizes, 1.0)
+    x, z, v = O.dis_admm(st, 0.05, 1.0, 3000)
+    for a0, a1 in zip(st.offsets[:-1], st.offsets[1:]):
+        gnz, gz = _kkt_gap(L.A[:, a0:a1], L.y, z[a0:a1], 0.05)
+        assert gnz < 1e-6 and gz < 1e-6
+    st1 = O.dis_setup(L.A, L.y, [80], 1.0)
+    xd, zd, vd = O.dis_admm(st1, 0.05, 1.0, 7)
+    xc, zc, vc = O.cen_admm(L.A, L.y, 0.05, 1.0, 7)
+    assert np.allclose(xd, xc, rtol=1e-11, atol=1e-12) and np.allclose(zd, zc, rtol=1e-11, atol=1e-12)
+
+
+def test_jacobi_schedule_reading():
+    # Eq. (loi32) taken literally (z^t, v^t from x^{t-1}) starting from zeros:
+    # round 1 leaves z = v = 0, and round 2 then performs the first
+    # Gauss-Seidel z/v update, so z_J^2 = z_GS^1 and v_J^2 = v_GS^1.
+    L = W.lasso_small(seed=7, M=30, N=40, nnz=4)
+    st = O.dis_setup(L.A, L.y, W.node_sizes(40, 2), 1.0)
+    x1, z1, v1 = O.dis_admm(st, 0.02, 1.0, 1, jacobi=True)
+    assert not z1.any() and not v1.any()
+    _, zj, vj = O.dis_admm(st, 0.02, 1.0, 2, jacobi=True)
+    xg, zg, vg = O.dis_admm(st, 0.02, 1.0, 1)
+    assert np.array_equal(x1, xg) and np.array_equal(zj, zg) and np.array_equal(vj, vg)
+
+
+def test_quantizers_definition():
+    qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+    S = 2 ** 24
+    u = np.array([-8.0, 8.0, 0.0, -7.999999, 1.5, 0.1])
+    q2 = O.gamma2(u, qp)
+    for ui, qi in zip(u, q2):
+        exact = (Fraction(float(ui)) - Fraction(-8)) * S
+        assert abs(Fraction(int(qi)) - exact) <= Fraction(1, 2)
+    assert q2[0] == 0 and q2[1] == qp.delta
+    # ties round to even: (u - zmin) * S = k + 1/2 exactly
+    tie = -8.0 + (5 + 0.5) / S
+    assert O.gamma2(np.array([tie]), qp)[0] == 6
+    tie2 = -8.0 + (6 + 0.5) / S
+    assert O.gamma2(np.array([tie2]), qp)[0] == 6
+    q1 = O.gamma1(np.array([0.25]), qp)
+    assert q1[0] == int((Fraction(0.25) + 8) * S * S)
+    with pytest.raises(ValueError):
+        O.gamma2(np.array([8.5]), qp)
+
+
+def test_decode_equals_exact_rational():
+    # x_i must be the float64 rounding of alpha~_i + sum_j B~_ij w~_j computed
+    # exactly from the dequantized inputs.
+    qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+    rng = np.random.default_rng(3)
+    Nk = 7
+    alpha = rng.standard_normal(Nk)
+    Bbar = rng.standard_normal((Nk, Nk)) * 0.3
+    z = rng.standard_normal(Nk)
+    v = rng.standard_normal(Nk)
+    c = O.gamma1(alpha, qp)
+    b = O.gamma2(Bbar, qp)
+    zq, vq = O.gamma2(z, qp), O.gamma2(-v, qp)
+    a = [int(x) + int(y) for x, y in zip(zq, vq)]
+    D = [int(c[i]) + sum(int(b[i, j]) * a[j] for j in range(Nk)) for i in range(Nk)]
+    x = O.decode(D, [int(s) for s in b.sum(axis=1)], sum(a), Nk, qp)
+    S = Fraction(2 ** 24)
+    for i in range(Nk):
+        at = Fraction(int(c[i])) / (S * S) + Fraction(-8)
+        val = at + sum((Fraction(int(b[i, j])) / S + Fraction(-8)) * (Fraction(a[j]) / S + 2 * Fraction(-8)) for j in range(Nk))
+        assert x[i] == float(val)
+
+
+def _setup_tiny(seed=11, N=12, K=2, M=10):
+    L = W.lasso_small(seed=seed, M=M, N=N, nnz=3, K=K)
+    st = O.dis_setup(L.A, L.y, W.node_sizes(N, K), 1.0)
+    return L, st
+
+
+def test_theorem1_private_equals_quantized():
+    L, st = _setup_tiny()
+    qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+    p, q = W.primes(256, 9)
+    key = P.derive_key(p, q)
+    pr = O.private_admm(st, 0.01, 1.0, 3, qp, key, seed=1234)
+    qz = O.quantized_admm(st, 0.01, 1.0, 3, qp)
+    for t in range(3):
+        assert pr.D[t] == qz.D[t]
+        assert np.array_equal(pr.x[t], qz.x[t])
+        assert np.array_equal(pr.z[t], qz.z[t]) and np.array_equal(pr.v[t], qz.v[t])
+        assert max(pr.D[t]) < key.n
+
+
+def round_error_bound(st, qp, z_prev, v_prev, x_priv):
+    """Per-round bound on |x_priv - x_plain| for the same (z, v) input:
+    1/(2 S^2) + sum_j (|w~_j| / (2S) + |Bbar_ij| / S) + one rounding."""
+    S = qp.S
+    zq, vq = O.gamma2(z_prev, qp), O.gamma2(-v_prev, qp)
+    wt = (zq + vq) / S + 2 * qp.zmin
+    eps = np.empty(len(x_priv))
+    for k, (a0, a1) in enumerate(zip(st.offsets[:-1], st.offsets[1:])):
+        for i in range(a1 - a0):
+            eps[a0 + i] = (0.5 / S ** 2 + np.sum(np.abs(wt[a0:a1]) / (2 * S) + np.abs(st.Bbar[k][i]) / S)
+                           + np.spacing(abs(x_priv[a0 + i])))
+    return eps
+
+
+def test_quantization_error_bound_and_mse():
+    L, st = _setup_tiny(seed=12, N=24, K=3, M=16)
+    qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+    T = 6
+    qz = O.quantized_admm(st, 0.01, 1.0, T, qp)
+    # plain Dis-ADMM trajectory
+    xs = []
+    for t in range(1, T + 1):
+        x, _, _ = O.dis_admm(st, 0.01, 1.0, t)
+        xs.append(x)
+    # round 1: same (z, v) = 0 input
+    eps1 = round_error_bound(st, qp, np.zeros(24), np.zeros(24), qz.x[0])
+    assert np.all(np.abs(qz.x[0] - xs[0]) <= eps1 + 1e-14)
+    # whole run: G_t <= 2 G_{t-1} + ||eps_t||, ||x_priv^T - x_plain^T|| <= G_{T-1} + ||eps_T||
+    G = 0.0
+    zp, vp = np.zeros(24), np.zeros(24)
+    for t in range(T):
+        e = np.linalg.norm(round_error_bound(st, qp, zp, vp, qz.x[t]))
+        bound_t = G + e
+        assert np.linalg.norm(qz.x[t] - xs[t]) <= bound_t + 1e-12
+        G = 2 * G + e
+        zp, vp = qz.z[t], qz.v[t]
+    dT = bound_t + 1e-12
+    mse_priv = np.mean((qz.x[-1] - L.x0) ** 2)
+    mse_plain = np.mean((xs[-1] - L.x0) ** 2)
+    assert abs(mse_priv - mse_plain) <= (2 * np.linalg.norm(xs[-1] - L.x0) * dT + dT ** 2) / 24
