@@ -1,0 +1,142 @@
+/*
+ * pc2.h -- C ABI of libpc2: batched Paillier encryption, decryption and
+ * homomorphic aggregation on one NVIDIA B300 (sm_103a), the data-parallel hot
+ * path of 3P-ADMM-PC2 (arXiv 2601.14980).
+ *
+ * Conventions (every entry point):
+ *  - Returns PC2_OK (0) or a negative PC2_E* code.  Argument errors are
+ *    reported at the call; errors found on the device (a plaintext >= n, a
+ *    quantizer input outside its range) set bits in the context's status
+ *    word, read and cleared by pc2_ctx_status().
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (for example
+ *    from torch tensors); h_* are host pointers.  Opaque objects (pc2_ctx,
+ *    pc2_key) are owned by the library and freed by their *_destroy call.
+ *  - Work is enqueued on the caller's stream and returns immediately.  Calls
+ *    that share one pc2_ctx must be ordered on one stream (they share its
+ *    scratch memory); use one context per concurrent stream.
+ *  - Big integers are little-endian arrays of 32-bit words.  Device vectors
+ *    of big integers use the TILED layout: 32-element tiles, each stored as
+ *    (limbs/4) slabs of 32 x 16-byte vectors; word j of element e is at
+ *        ((e/32) * (limbs/4) + j/4) * 128 + (e%32) * 4 + j%4.
+ *    A tiled buffer of `count` elements holds pc2_tiled_words(count, limbs)
+ *    words.  pc2_pack / pc2_unpack convert from / to the canonical layout
+ *    (element e at words [e*limbs, (e+1)*limbs)).
+ *  - Key sizes: n of 256, 512, 1024, 2048 or 3072 bits.  Plaintexts have
+ *    nbits/32 limbs, ciphertexts nbits/16 limbs.
+ *  - Scratch: a context owns device scratch memory and grows it on the first
+ *    call that needs more (cudaMalloc; synchronises the device).  Call
+ *    pc2_ctx_reserve() first to avoid growth inside timed regions or stream
+ *    capture.
+ */
+#ifndef PC2_H
+#define PC2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pc2_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+enum {
+  PC2_OK = 0,
+  PC2_EINVAL = -1,      /* bad argument (null pointer, unsupported size, ...) */
+  PC2_ERANGE = -2,      /* a value outside the range the operation accepts */
+  PC2_EKEY = -3,        /* private-key operation on a public key, or an invalid key */
+  PC2_ENOMEM = -4,      /* device or host allocation failed */
+  PC2_ECUDA = -5,       /* a CUDA call failed */
+  PC2_ETIMEOUT = -6,    /* a bounded wait ran out */
+  PC2_EMISSING = -7,    /* an expected input was not supplied */
+  PC2_EUNSUPPORTED = -8 /* a configuration the library does not implement */
+};
+
+/* Status-word bits set by kernels (pc2_ctx_status). */
+enum { PC2_ST_RANGE = 1, PC2_ST_QUANT = 2, PC2_ST_TIMEOUT = 4 };
+
+typedef struct pc2_ctx pc2_ctx;
+typedef struct pc2_key pc2_key;
+
+const char* pc2_strerror(int code);
+
+/* ---- context --------------------------------------------------------- */
+/* Creates a context on CUDA device `device` (makes it current). */
+int pc2_ctx_create(int device, pc2_ctx** out);
+void pc2_ctx_destroy(pc2_ctx* ctx);
+/* Grows the context's scratch to at least `bytes` now (synchronises). */
+int pc2_ctx_reserve(pc2_ctx* ctx, size_t bytes);
+/* Bytes of scratch currently held. */
+size_t pc2_ctx_scratch_bytes(const pc2_ctx* ctx);
+/* Synchronises `stream`, returns the PC2_ST_* bits raised since the last call in *bits, clears them. */
+int pc2_ctx_status(pc2_ctx* ctx, pc2_stream_t stream, int* bits);
+/* Forces the sliding-window width (3..6) of subsequent exponentiations; 0 = automatic. */
+int pc2_ctx_set_window(pc2_ctx* ctx, int w);
+
+/* ---- keys (host) ------------------------------------------------------ *
+ * Sec. III-B: n = pq, lambda = lcm(p-1, q-1), g = n + 1 (so g^m = 1 + mn and
+ * mu = lambda^-1 mod n).  Key generation is deterministic in `seed`: primes of
+ * nbits/2 bits with the top two bits set, from a Philox4x32-10 stream, sieved
+ * and checked by 32 Miller-Rabin rounds. */
+int pc2_keygen(int nbits, uint64_t seed, pc2_key** out);
+/* A private key from given primes (each `words` words, equal bit length
+ * nbits/2); rejects composites (Miller-Rabin), p == q, or gcd(n, lambda) != 1. */
+int pc2_key_from_primes(const uint32_t* h_p, const uint32_t* h_q, int words, pc2_key** out);
+/* A public copy (n, g only) of a key. */
+int pc2_key_public(const pc2_key* key, pc2_key** out);
+void pc2_key_destroy(pc2_key* key);
+/* nbits and whether the key holds the private part. */
+int pc2_key_info(const pc2_key* key, int* nbits, int* has_private);
+/* Exports n (nbits/32 words); for private keys also p, q (p < q; nbits/64
+ * words each), lambda and mu (nbits/32 words each).  Any pointer may be NULL. */
+int pc2_key_export(const pc2_key* key, uint32_t* h_n, uint32_t* h_p, uint32_t* h_q, uint32_t* h_lambda, uint32_t* h_mu);
+/* Montgomery products one call costs per element (for throughput accounting):
+ * op 0 = pc2_encrypt (key owner, CRT), 1 = public encryption, 2 = decryption;
+ * *limbs receives the operand width of those products. */
+int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, int* limbs);
+
+/* ---- layout ----------------------------------------------------------- */
+size_t pc2_tiled_words(size_t count, int limbs);
+int pc2_pack(pc2_ctx* ctx, const uint32_t* d_canon, size_t count, int limbs, uint32_t* d_tiled, pc2_stream_t stream);
+int pc2_unpack(pc2_ctx* ctx, const uint32_t* d_tiled, size_t count, int limbs, uint32_t* d_canon, pc2_stream_t stream);
+
+/* ---- Paillier ---------------------------------------------------------- *
+ * Encryption, Eq. (itq1): c = g^m r^n mod n^2 with g = n + 1.  The random r of
+ * element e (0-based in this call) is r_raw mod n, where r_raw is the
+ * (nbits/32 + 2)-word integer whose word 4j+i is output i of Philox4x32-10
+ * for counter (j, E_lo, E_hi, stream) and key (seed_lo, seed_hi), E = e0 + e.
+ * (Only r mod n matters: (r + tn)^n = r^n mod n^2.)
+ * d_m: `count` uint64 plaintexts.  d_ct: tiled, nbits/16 limbs.
+ * With a private key the work runs through the CRT split of Sec. IV-A
+ * (Lemmas 1-2, Eq. (gA-C-B)); with a public key directly mod n^2.  Both
+ * give the same ciphertext. */
+int pc2_encrypt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed, uint32_t stream,
+                uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream);
+/* As pc2_encrypt, plaintexts of full width: d_m tiled, nbits/32 limbs, each m < n
+ * (m >= n raises PC2_ST_RANGE). */
+int pc2_encrypt_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_m, size_t count, uint64_t seed,
+                     uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream);
+/* Public-key encryption mod n^2 even when the key is private (same result as pc2_encrypt). */
+int pc2_encrypt_public(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
+                       uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream);
+/* Decryption, Sec. III-C: m = L(c^lambda mod n^2) mu mod n, computed through
+ * the CRT (m_p = L_p(c^(p-1) mod p^2) h_p mod p, likewise for q, then Garner).
+ * d_ct: tiled, nbits/16 limbs; d_m: tiled, nbits/32 limbs.  PC2_EKEY for a public key. */
+int pc2_decrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_m,
+                pc2_stream_t cstream);
+/* Definition 1 (Eq. (headd)): d_out = d_a * d_b mod n^2 (encrypts a + b mod n). */
+int pc2_hom_add(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_a, const uint32_t* d_b, size_t count,
+                uint32_t* d_out, pc2_stream_t cstream);
+/* Definition 1 over `groups` operands: d_out[i] = prod_g d_ct[g][i] mod n^2.
+ * d_ct holds the groups back to back, each a tiled array of `count` ciphertexts
+ * (group g starts at word g * pc2_tiled_words(count, nbits/16)). */
+int pc2_hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t groups, size_t count, uint32_t* d_out,
+                pc2_stream_t cstream);
+/* Definition 2 (Eq. (hemul)): d_out[i] = d_ct[i]^k[i] mod n^2 (encrypts k m mod n). */
+int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint64_t* d_k, size_t count,
+                 uint32_t* d_out, pc2_stream_t cstream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC2_H */

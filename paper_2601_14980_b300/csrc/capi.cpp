@@ -1,0 +1,438 @@
+// capi.cpp -- the extern "C" entry points of libpc2 (include/pc2.h).
+//
+// Marshals arguments, builds (and caches per key) the kernels' parameter
+// blocks, owns the per-context scratch memory, and dispatches on the key size
+// to the templated launchers.  No arithmetic on user data happens here.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <utility>
+
+#include "../../include/pc2.h"
+#include "keys.hpp"
+#include "philox.h"
+#include "pc2_kernels.h"
+
+struct pc2_ctx {
+  int device = 0;
+  int sms = 0;
+  uint32_t* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int* status = nullptr;  // device word of PC2_ST_* bits
+  int window = 0;         // 0 = automatic
+};
+
+namespace pc2 {
+
+// Parameter blocks cached per (key, kind, window): building them needs
+// host big-integer work (inverses, schedules) that must stay off the hot path.
+struct ParamCache {
+  std::mutex mu;
+  std::map<std::pair<const pc2_key*, int>, std::shared_ptr<void>> blocks;
+};
+static ParamCache& cache() {
+  static ParamCache c;
+  return c;
+}
+static void cache_drop(const pc2_key* k) {
+  std::lock_guard<std::mutex> g(cache().mu);
+  for (auto it = cache().blocks.begin(); it != cache().blocks.end();)
+    it = it->first.first == k ? cache().blocks.erase(it) : std::next(it);
+}
+
+template <class P, class F>
+static std::shared_ptr<P> cached(const pc2_key* k, int kind, int window, F make, int* rc) {
+  const int tag = kind * 16 + window;
+  {
+    std::lock_guard<std::mutex> g(cache().mu);
+    auto it = cache().blocks.find({k, tag});
+    if (it != cache().blocks.end()) {
+      *rc = PC2_OK;
+      return std::static_pointer_cast<P>(it->second);
+    }
+  }
+  std::shared_ptr<P> p(new (std::nothrow) P);
+  if (!p) { *rc = PC2_ENOMEM; return nullptr; }
+  *rc = make(*p);
+  if (*rc != PC2_OK) return nullptr;
+  std::lock_guard<std::mutex> g(cache().mu);
+  cache().blocks[{k, tag}] = p;
+  return p;
+}
+
+enum { KIND_ENC_CRT = 1, KIND_ENC_PUB = 2, KIND_DEC = 3 };
+
+static uint32_t* ctx_scratch(void* c, size_t bytes) {
+  pc2_ctx* ctx = static_cast<pc2_ctx*>(c);
+  if (bytes <= ctx->scratch_bytes) return ctx->scratch;
+  if (pc2_ctx_reserve(ctx, bytes) != PC2_OK) return nullptr;
+  return ctx->scratch;
+}
+
+template <int Lh>
+static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
+                   uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
+  int rc;
+  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, ctx->window,
+                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, ctx->window, P); }, &rc);
+  if (!P0) return rc;
+  std::unique_ptr<EncCrtParams<Lh>> P(new (std::nothrow) EncCrtParams<Lh>(*P0));
+  if (!P) return PC2_ENOMEM;
+  P->seed = seed;
+  P->stream = stream;
+  P->e0 = e0;
+  P->mwords = mw ? Lh : 2;
+  return launch_enc_crt<Lh, lanes_for(Lh)>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+}
+
+template <int L2>
+static int enc_pub(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
+                   uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
+  int rc;
+  auto P0 = cached<EncPubParams<L2>>(key, KIND_ENC_PUB, ctx->window,
+                                     [&](EncPubParams<L2>& P) { return make_enc_pub<L2>(*key, ctx->window, P); }, &rc);
+  if (!P0) return rc;
+  std::unique_ptr<EncPubParams<L2>> P(new (std::nothrow) EncPubParams<L2>(*P0));
+  if (!P) return PC2_ENOMEM;
+  P->seed = seed;
+  P->stream = stream;
+  P->e0 = e0;
+  P->mwords = mw ? L2 / 2 : 2;
+  return launch_enc_pub<L2, lanes_for(L2)>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+}
+
+template <int Lh>
+static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st) {
+  int rc;
+  auto P = cached<DecParams<Lh>>(key, KIND_DEC, ctx->window,
+                                 [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, ctx->window, p); }, &rc);
+  if (!P) return rc;
+  return launch_dec_crt<Lh, lanes_for(Lh)>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st);
+}
+
+template <int L2>
+static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs, size_t groups, size_t count,
+                   uint32_t* out, cudaStream_t st) {
+  // chunks of at most kMaxGroups operands; later chunks start from the running product
+  size_t done = 0;
+  bool first = true;
+  while (done < groups) {
+    std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>);
+    if (!P) return PC2_ENOMEM;
+    int k = 0;
+    const uint32_t* ops[kMaxGroups];
+    if (!first) ops[k++] = out;
+    while (k < kMaxGroups && done < groups) ops[k++] = srcs[done++];
+    int rc = make_hom<L2>(*key, ctx->window, k, *P);
+    if (rc) return rc;
+    for (int i = 0; i < k; ++i) P->src[i] = ops[i];
+    rc = launch_hom_sum<L2, lanes_for(L2)>(*P, count, out, ctx->sms, st);
+    if (rc) return rc;
+    first = false;
+  }
+  return PC2_OK;
+}
+
+template <int L2>
+static int hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, const uint64_t* k, size_t count,
+                    uint32_t* out, cudaStream_t st) {
+  std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>);
+  if (!P) return PC2_ENOMEM;
+  int rc = make_hom<L2>(*key, ctx->window ? (ctx->window > 5 ? 5 : ctx->window) : 4, 1, *P);
+  if (rc) return rc;
+  return launch_hom_scal<L2, lanes_for(L2)>(*P, ct, k, count, out, ctx_scratch, ctx, ctx->sms, st);
+}
+
+}  // namespace pc2
+
+using namespace pc2;
+
+#define PC2_DISPATCH_H(Lh, call) \
+  switch (Lh) {                  \
+    case 8: return call(8);      \
+    case 16: return call(16);    \
+    case 32: return call(32);    \
+    case 64: return call(64);    \
+    case 96: return call(96);    \
+    default: return PC2_EUNSUPPORTED; \
+  }
+
+extern "C" {
+
+const char* pc2_strerror(int code) {
+  switch (code) {
+    case PC2_OK: return "ok";
+    case PC2_EINVAL: return "invalid argument";
+    case PC2_ERANGE: return "value out of range";
+    case PC2_EKEY: return "invalid key or private-key operation on a public key";
+    case PC2_ENOMEM: return "out of memory";
+    case PC2_ECUDA: return "CUDA error";
+    case PC2_ETIMEOUT: return "timed out";
+    case PC2_EMISSING: return "missing input";
+    case PC2_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+int pc2_ctx_create(int device, pc2_ctx** out) {
+  if (!out) return PC2_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return PC2_ECUDA;
+  std::unique_ptr<pc2_ctx> c(new (std::nothrow) pc2_ctx);
+  if (!c) return PC2_ENOMEM;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PC2_ECUDA;
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess) return PC2_ENOMEM;
+  if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return PC2_ECUDA;
+  *out = c.release();
+  return PC2_OK;
+}
+
+void pc2_ctx_destroy(pc2_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->status) cudaFree(ctx->status);
+  delete ctx;
+}
+
+int pc2_ctx_reserve(pc2_ctx* ctx, size_t bytes) {
+  if (!ctx) return PC2_EINVAL;
+  if (bytes <= ctx->scratch_bytes) return PC2_OK;
+  const size_t gran = (size_t)64 << 20;
+  bytes = (bytes + gran - 1) / gran * gran;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return PC2_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PC2_ECUDA;  // earlier users of the old buffer
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+    ctx->scratch = nullptr;
+    return PC2_ENOMEM;
+  }
+  ctx->scratch_bytes = bytes;
+  return PC2_OK;
+}
+
+size_t pc2_ctx_scratch_bytes(const pc2_ctx* ctx) { return ctx ? ctx->scratch_bytes : 0; }
+
+int pc2_ctx_status(pc2_ctx* ctx, pc2_stream_t stream, int* bits) {
+  if (!ctx || !bits) return PC2_EINVAL;
+  int v = 0;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PC2_ECUDA;
+  if (cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PC2_ECUDA;
+  if (cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return PC2_ECUDA;
+  *bits = v;
+  return PC2_OK;
+}
+
+int pc2_ctx_set_window(pc2_ctx* ctx, int w) {
+  if (!ctx || (w != 0 && (w < 3 || w > kMaxWin))) return PC2_EINVAL;
+  ctx->window = w;
+  return PC2_OK;
+}
+
+int pc2_keygen(int nbits, uint64_t seed, pc2_key** out) {
+  if (!out || !supported_nbits(nbits)) return PC2_EINVAL;
+  *out = nullptr;
+  const int half = nbits / 2;
+  Big pr[2];
+  uint32_t cand = 0;
+  for (int which = 0; which < 2;) {
+    Big x;
+    x.w.assign((size_t)half / 32, 0);
+    for (size_t j = 0; j < x.w.size(); j += 4) {
+      const U4 v = philox4x32_10(U4{(uint32_t)j, cand, (uint32_t)nbits, 0x6B657967u}, (uint32_t)seed,
+                                 (uint32_t)(seed >> 32));
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+      for (int i = 0; i < 4 && j + i < x.w.size(); ++i) x.w[j + i] = w4[i];
+    }
+    ++cand;
+    x.w.back() |= 0xC0000000u;  // top two bits: p q has exactly nbits bits
+    x.w[0] |= 1u;
+    if (!probable_prime(x, 32, seed ^ cand)) continue;
+    if (which == 1 && cmp(x, pr[0]) == 0) continue;
+    pr[which++] = x;
+  }
+  return key_from_primes(pr[0], pr[1], out);
+}
+
+int pc2_key_from_primes(const uint32_t* h_p, const uint32_t* h_q, int words, pc2_key** out) {
+  if (!h_p || !h_q || words <= 0 || !out) return PC2_EINVAL;
+  *out = nullptr;
+  try {
+    return key_from_primes(Big::from_words(h_p, (size_t)words), Big::from_words(h_q, (size_t)words), out);
+  } catch (...) {
+    return PC2_EINVAL;
+  }
+}
+
+int pc2_key_public(const pc2_key* key, pc2_key** out) {
+  if (!key || !out) return PC2_EINVAL;
+  std::unique_ptr<pc2_key> k(new (std::nothrow) pc2_key);
+  if (!k) return PC2_ENOMEM;
+  k->nbits = key->nbits;
+  k->Lh = key->Lh;
+  k->priv = false;
+  k->n = key->n;
+  k->n2 = key->n2;
+  *out = k.release();
+  return PC2_OK;
+}
+
+void pc2_key_destroy(pc2_key* key) {
+  if (!key) return;
+  cache_drop(key);
+  delete key;
+}
+
+int pc2_key_info(const pc2_key* key, int* nbits, int* has_private) {
+  if (!key) return PC2_EINVAL;
+  if (nbits) *nbits = key->nbits;
+  if (has_private) *has_private = key->priv ? 1 : 0;
+  return PC2_OK;
+}
+
+int pc2_key_export(const pc2_key* key, uint32_t* h_n, uint32_t* h_p, uint32_t* h_q, uint32_t* h_lambda, uint32_t* h_mu) {
+  if (!key) return PC2_EINVAL;
+  if (h_n) key->n.to_words(h_n, key->Lh);
+  if ((h_p || h_q || h_lambda || h_mu) && !key->priv) return PC2_EKEY;
+  if (h_p) key->p.to_words(h_p, key->Lh / 2);
+  if (h_q) key->q.to_words(h_q, key->Lh / 2);
+  if (h_lambda) key->lambda.to_words(h_lambda, key->Lh);
+  if (h_mu) key->mu.to_words(h_mu, key->Lh);
+  return PC2_OK;
+}
+
+int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, int* limbs) {
+  if (!ctx || !key || !montmuls || !limbs) return PC2_EINVAL;
+  const int w = ctx->window;
+  int rc = PC2_OK;
+  auto fill = [&](auto tag) -> int {
+    constexpr int Lh = decltype(tag)::value;
+    if (op == 0) {
+      auto P = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w, [&](EncCrtParams<Lh>& p) { return make_enc_crt<Lh>(*key, w, p); }, &rc);
+      if (!P) return rc;
+      *montmuls = (long)P->ep.montmuls + P->eq.montmuls;
+      *limbs = Lh;
+    } else if (op == 1) {
+      auto P = cached<EncPubParams<2 * Lh>>(key, KIND_ENC_PUB, w, [&](EncPubParams<2 * Lh>& p) { return make_enc_pub<2 * Lh>(*key, w, p); }, &rc);
+      if (!P) return rc;
+      *montmuls = (long)P->e.montmuls + 1;
+      *limbs = 2 * Lh;
+    } else if (op == 2) {
+      auto P = cached<DecParams<Lh>>(key, KIND_DEC, w, [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, w, p); }, &rc);
+      if (!P) return rc;
+      *montmuls = (long)P->ep.montmuls + P->eq.montmuls;
+      *limbs = Lh;
+    } else {
+      return PC2_EINVAL;
+    }
+    return PC2_OK;
+  };
+  switch (key->Lh) {
+    case 8: return fill(std::integral_constant<int, 8>());
+    case 16: return fill(std::integral_constant<int, 16>());
+    case 32: return fill(std::integral_constant<int, 32>());
+    case 64: return fill(std::integral_constant<int, 64>());
+    case 96: return fill(std::integral_constant<int, 96>());
+    default: return PC2_EUNSUPPORTED;
+  }
+}
+
+size_t pc2_tiled_words(size_t count, int limbs) { return (count + 31) / 32 * 32 * (size_t)limbs; }
+
+int pc2_pack(pc2_ctx* ctx, const uint32_t* d_canon, size_t count, int limbs, uint32_t* d_tiled, pc2_stream_t stream) {
+  if (!ctx || limbs <= 0 || limbs % 4 || (count && (!d_canon || !d_tiled))) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  return launch_pack(d_canon, count, limbs, d_tiled, ctx->sms, (cudaStream_t)stream);
+}
+
+int pc2_unpack(pc2_ctx* ctx, const uint32_t* d_tiled, size_t count, int limbs, uint32_t* d_canon, pc2_stream_t stream) {
+  if (!ctx || limbs <= 0 || limbs % 4 || (count && (!d_canon || !d_tiled))) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  return launch_unpack(d_tiled, count, limbs, d_canon, ctx->sms, (cudaStream_t)stream);
+}
+
+static int encrypt_any(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
+                       uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cs, bool force_pub) {
+  if (!ctx || !key || !d_ct || (!m64 && !mw)) return count ? PC2_EINVAL : PC2_OK;
+  if (!count) return PC2_OK;
+  const cudaStream_t st = (cudaStream_t)cs;
+  if (key->priv && !force_pub) {
+#define PC2_CALL_CRT(L) enc_crt<L>(ctx, key, m64, mw, count, seed, stream, e0, d_ct, st)
+    PC2_DISPATCH_H(key->Lh, PC2_CALL_CRT)
+  }
+#define PC2_CALL_PUB(L) enc_pub<2 * L>(ctx, key, m64, mw, count, seed, stream, e0, d_ct, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_PUB)
+}
+
+int pc2_encrypt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed, uint32_t stream,
+                uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream) {
+  if (count && !d_m) return PC2_EINVAL;
+  return encrypt_any(ctx, key, d_m, nullptr, count, seed, stream, e0, d_ct, cstream, false);
+}
+
+int pc2_encrypt_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_m, size_t count, uint64_t seed,
+                     uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream) {
+  if (count && !d_m) return PC2_EINVAL;
+  return encrypt_any(ctx, key, nullptr, d_m, count, seed, stream, e0, d_ct, cstream, false);
+}
+
+int pc2_encrypt_public(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
+                       uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cstream) {
+  if (count && !d_m) return PC2_EINVAL;
+  return encrypt_any(ctx, key, d_m, nullptr, count, seed, stream, e0, d_ct, cstream, true);
+}
+
+int pc2_decrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_m,
+                pc2_stream_t cstream) {
+  if (!ctx || !key) return PC2_EINVAL;
+  if (!key->priv) return PC2_EKEY;
+  if (!count) return PC2_OK;
+  if (!d_ct || !d_m) return PC2_EINVAL;
+  const cudaStream_t st = (cudaStream_t)cstream;
+#define PC2_CALL_DEC(L) dec<L>(ctx, key, d_ct, count, d_m, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_DEC)
+}
+
+int pc2_hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t groups, size_t count, uint32_t* d_out,
+                pc2_stream_t cstream) {
+  if (!ctx || !key || groups == 0) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  if (!d_ct || !d_out) return PC2_EINVAL;
+  std::unique_ptr<const uint32_t*[]> srcs(new (std::nothrow) const uint32_t*[groups]);
+  if (!srcs) return PC2_ENOMEM;
+  const size_t stride = pc2_tiled_words(count, 2 * key->Lh);
+  for (size_t g = 0; g < groups; ++g) srcs[g] = d_ct + g * stride;
+  const cudaStream_t st = (cudaStream_t)cstream;
+#define PC2_CALL_SUM(L) hom_sum<2 * L>(ctx, key, srcs.get(), groups, count, d_out, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_SUM)
+}
+
+int pc2_hom_add(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_a, const uint32_t* d_b, size_t count,
+                uint32_t* d_out, pc2_stream_t cstream) {
+  if (!ctx || !key) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  if (!d_a || !d_b || !d_out) return PC2_EINVAL;
+  const uint32_t* srcs[2] = {d_a, d_b};
+  const cudaStream_t st = (cudaStream_t)cstream;
+#define PC2_CALL_ADD(L) hom_sum<2 * L>(ctx, key, srcs, 2, count, d_out, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_ADD)
+}
+
+int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint64_t* d_k, size_t count,
+                 uint32_t* d_out, pc2_stream_t cstream) {
+  if (!ctx || !key) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  if (!d_ct || !d_k || !d_out) return PC2_EINVAL;
+  const cudaStream_t st = (cudaStream_t)cstream;
+#define PC2_CALL_SCAL(L) hom_scal<2 * L>(ctx, key, d_ct, d_k, count, d_out, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_SCAL)
+}
+
+}  // extern "C"

@@ -1,0 +1,505 @@
+// paillier_kernels.cu -- the Paillier kernels of libpc2 and their launchers.
+//
+//   k_enc_crt  key-owner encryption, Eq. (itq1) evaluated through the CRT
+//              split of Sec. IV-A: r^n mod p^2 and mod q^2 with the exponent
+//              reduced mod phi(p^2), phi(q^2) (Lemma 1), each half times
+//              g^m = 1 + m n, recombined by Eq. (gA-C-B) (Lemma 2).
+//   k_enc_pub  public-key encryption, Eq. (itq1) directly mod n^2.
+//   k_dec_crt  decryption of Sec. III-C via the CRT: m_p = L_p(c^(p-1) mod p^2) h_p
+//              mod p, m_q likewise, Garner recombination mod n (equal to
+//              L(c^lambda mod n^2) mu mod n; Sec. IV-A notes the same CRT
+//              acceleration applies to c^lambda).
+//   k_hom_sum  Definition 1 over several operands: prod_g c_g mod n^2.
+//   k_hom_scal Definition 2: c^k mod n^2, per-element k < 2^64.
+//
+// All modexp kernels are persistent: a grid of (SMs x resident CTAs) walks the
+// elements; each element is owned by a group of T lanes (mont.cuh).  Scratch
+// (global memory, from the context) holds each group's window table and glue
+// columns, interleaved by group so that a warp's accesses coalesce.
+#include <cuda_runtime.h>
+
+#include "mont.cuh"
+#include "pc2_kernels.h"
+#include "philox.h"
+
+namespace pc2 {
+
+// Resident CTAs per SM each kernel is compiled for: the register budget of
+// 65536 / (128 * blocks) must hold two limb segments (three when the modulus
+// segment lives in registers, T > 1) plus bookkeeping.  Keeping the budget
+// tight stops the compiler from hoisting the modulus words (constant-bank
+// operands) into registers.
+constexpr int min_blocks(int L, int T) {
+  const int S = L / T;
+  const int regs = (T == 1 ? 2 * S : 3 * S) + 24;
+  const int b = 65536 / (kThreads * regs);
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
+// ------------------------------------------------------------------ helpers
+template <int S, int T, int MAXS>
+__device__ __forceinline__ void run_modexp(uint32_t (&a)[S], const Sched<MAXS>& E, const uint32_t* n, uint32_t np,
+                                           const Col& tab, const Col& bsh, const Grp<T>& g) {
+  if constexpr (T == 1) {
+    modexp_sched<S, T>(a, E, tab, bsh, ParamN{n}, np, g);
+  } else {
+    const RegN<S> rn = reg_n<S, T>(n, g);
+    modexp_sched<S, T>(a, E, tab, bsh, rn, np, g);
+  }
+}
+
+// r_raw for element e: `words` Philox words, zero-padded to `total`.
+__device__ __forceinline__ void gen_r(const Col& X, uint64_t seed, uint32_t stream, uint64_t e, int words, int total) {
+  for (int j4 = 0; 4 * j4 < words; ++j4) {
+    const U4 v = r_block(seed, stream, e, (uint32_t)j4);
+    const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (4 * j4 + i < words) X[4 * j4 + i] = w4[i];
+  }
+  for (int j = words; j < total; ++j) X[j] = 0u;
+}
+
+// GM = 1 + m n (zero-padded to `total` words); m from uint64 input or a tiled
+// wide input of Ln limbs.  Flags PC2_ST_RANGE when a wide m >= n.
+__device__ __forceinline__ void make_gm(const Col& GM, const Col& M, const uint64_t* m64, const uint32_t* mwide,
+                                        size_t e, const uint32_t* n, int Ln, int total, bool valid, int* status) {
+  int mw;
+  if (mwide) {
+    for (int j = 0; j < Ln; ++j) M[j] = mwide[tiled_index(e, j, Ln)];
+    mw = Ln;
+    if (valid && g_ge(M, PArr{n}, Ln)) atomicOr(status, PC2_ST_RANGE);
+  } else {
+    const uint64_t m = m64[e];
+    M[0] = (uint32_t)m;
+    M[1] = (uint32_t)(m >> 32);
+    mw = 2;
+  }
+  g_mul(GM, M, mw, PArr{n}, Ln);
+  uint64_t c = 1;
+  for (int j = 0; j < mw + Ln; ++j) {
+    c += GM[j];
+    GM[j] = (uint32_t)c;
+    c >>= 32;
+  }
+  for (int j = mw + Ln; j < total; ++j) GM[j] = 0u;
+}
+
+// Writes words [0, Lc) of column V as element e of a tiled output; lane k of
+// the group writes its share of the words.
+template <int T>
+__device__ __forceinline__ void write_tiled(uint32_t* out, size_t e, const Col& V, int Lc, const Grp<T>& g) {
+  const int per = Lc / T;
+  for (int j = g.k * per; j < (g.k + 1) * per; ++j) out[tiled_index(e, j, Lc)] = V[j];
+}
+
+struct Layout {
+  int G, gl, Gtot, gg;
+  __device__ Layout(int T) {
+    G = (int)blockDim.x / T;
+    gl = (int)threadIdx.x / T;
+    Gtot = (int)gridDim.x * G;
+    gg = (int)blockIdx.x * G + gl;
+  }
+  __device__ __forceinline__ Col slot(uint32_t* scratch, size_t first_word) const {
+    return Col{scratch + first_word * (size_t)Gtot + gg, Gtot};
+  }
+};
+
+// ------------------------------------------------------------------ CRT encryption
+template <int Lh, int T>
+__device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMaxSched>& E, const Col& X, const Col& GM,
+                                         const Col& OUT, const Col& A, const Col& B, const Col& C, const Col& TT,
+                                         const Col& tab, const Col& bsh, const Grp<T>& g) {
+  constexpr int S = Lh / T;
+  g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // r~ = r R mod h^2
+  __syncwarp();
+  uint32_t a[S];
+  load_seg(a, A, g);
+  run_modexp<S, T>(a, E, M.n, M.np, tab, bsh, g);          // (r^n mod h^2) R
+  store_seg(A, a, g);
+  __syncwarp();
+  g_to_mont_2l(B, GM, M.n, M.r2, M.r3, M.np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
+  g_mont(C, A, B, M.n, M.np, Lh, TT);                          // c_h R
+  g_zero(B, Lh);
+  B[0] = 1u;
+  g_mont(OUT, C, B, M.n, M.np, Lh, TT);                        // c_h
+}
+
+template <int Lh, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const __grid_constant__ EncCrtParams<Lh> P,
+                                                      const uint64_t* __restrict__ m64,
+                                                      const uint32_t* __restrict__ mwide, size_t count,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
+                                                      int tabw, int* status) {
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  const int SW = 2 * Lh + 4;
+  const Col X = ly.slot(scratch, tabw + 0 * SW), GM = ly.slot(scratch, tabw + 1 * SW),
+            A = ly.slot(scratch, tabw + 2 * SW), B = ly.slot(scratch, tabw + 3 * SW),
+            C = ly.slot(scratch, tabw + 4 * SW), TT = ly.slot(scratch, tabw + 5 * SW),
+            CP = ly.slot(scratch, tabw + 6 * SW), CQ = ly.slot(scratch, tabw + 7 * SW);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    gen_r(X, P.seed, P.stream, P.e0 + e, Lh + 2, 2 * Lh);
+    make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid, status);
+    enc_half<Lh, T>(P.mp, P.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
+    enc_half<Lh, T>(P.mq, P.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
+    // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2  (c_p < p^2 < q^2)
+    if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
+    g_copy_param(B, P.pinv2R, Lh);
+    g_mont(C, A, B, P.mq.n, P.mq.np, Lh, TT);
+    g_mul(X, C, Lh, PArr{P.p2}, Lh);
+    uint64_t c = 0;
+    for (int j = 0; j < 2 * Lh; ++j) {
+      c += (uint64_t)X[j] + (j < Lh ? CP[j] : 0u);
+      X[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    if (valid) write_tiled<T>(out, e, X, 2 * Lh, g);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ public-key encryption
+template <int L2, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_enc_pub(const __grid_constant__ EncPubParams<L2> P,
+                                                      const uint64_t* __restrict__ m64,
+                                                      const uint32_t* __restrict__ mwide, size_t count,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
+                                                      int tabw, int* status) {
+  constexpr int S = L2 / T, Ln = L2 / 2;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  const int SW = L2 + 4;
+  const Col X = ly.slot(scratch, tabw + 0 * SW), GM = ly.slot(scratch, tabw + 1 * SW),
+            A = ly.slot(scratch, tabw + 2 * SW), TT = ly.slot(scratch, tabw + 3 * SW);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    gen_r(X, P.seed, P.stream, P.e0 + e, Ln + 2, L2);
+    __syncwarp();
+    uint32_t a[S];
+    load_seg(a, X, g);
+    // r~ = r R mod n^2  (r_raw < R)
+#pragma unroll
+    for (int j = 0; j < S; ++j) bsh[g.k * S + j] = P.m.r2[g.k * S + j];
+    __syncwarp();
+    if constexpr (T == 1) {
+      mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+    } else {
+      const RegN<S> rn = reg_n<S, T>(P.m.n, g);
+      mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+    }
+    __syncwarp();
+    run_modexp<S, T>(a, P.e, P.m.n, P.m.np, tab, bsh, g);  // (r^n) R
+    store_seg(A, a, g);
+    __syncwarp();
+    make_gm(GM, X, m64, mwide, e, P.nwords, Ln, L2, valid, status);
+    g_mont(X, A, GM, P.m.n, P.m.np, L2, TT);  // r^n (1 + m n) mod n^2
+    if (valid) write_tiled<T>(out, e, X, L2, g);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ CRT decryption
+template <int Lh, int T>
+__device__ __forceinline__ void dec_half(const ModConst<Lh>& M, const Sched<kMaxSchedHalf>& E, const uint32_t* h,
+                                         uint32_t hnp, const uint32_t* hinvlo, const uint32_t* hhR, const Col& X,
+                                         const Col& OUT, const Col& A, const Col& B, const Col& C, const Col& TT,
+                                         const Col& tab, const Col& bsh, const Grp<T>& g) {
+  constexpr int S = Lh / T, Lp = Lh / 2;
+  g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // c R mod h^2
+  __syncwarp();
+  uint32_t a[S];
+  load_seg(a, A, g);
+  run_modexp<S, T>(a, E, M.n, M.np, tab, bsh, g);          // c^(h-1) R mod h^2
+  store_seg(A, a, g);
+  __syncwarp();
+  g_zero(B, Lh);
+  B[0] = 1u;
+  g_mont(C, A, B, M.n, M.np, Lh, TT);  // x = c^(h-1) mod h^2, x = 1 mod h
+  // x - 1 (x >= 1)
+  {
+    uint64_t br = 1;
+    for (int j = 0; j < Lh && br; ++j) {
+      const uint32_t v = C[j];
+      C[j] = v - 1u;
+      br = (v == 0u);
+    }
+  }
+  g_mul_lo(A, C, PArr{hinvlo}, Lp);   // L_h(x) = (x-1)/h exactly, via h^-1 mod 2^(32 Lp)
+  g_copy_param(B, hhR, Lp);
+  g_mont(OUT, A, B, h, hnp, Lp, TT);  // m_h = L_h(x) h_h mod h
+}
+
+template <int Lh, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const __grid_constant__ DecParams<Lh> P,
+                                                      const uint32_t* __restrict__ ct, size_t count,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
+                                                      int tabw) {
+  constexpr int Lp = Lh / 2;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  const int SW = 2 * Lh + 4;
+  const Col X = ly.slot(scratch, tabw + 0 * SW), A = ly.slot(scratch, tabw + 1 * SW),
+            B = ly.slot(scratch, tabw + 2 * SW), C = ly.slot(scratch, tabw + 3 * SW),
+            TT = ly.slot(scratch, tabw + 4 * SW), MP = ly.slot(scratch, tabw + 5 * SW),
+            MQ = ly.slot(scratch, tabw + 6 * SW);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(e, j, 2 * Lh)];
+    dec_half<Lh, T>(P.mp, P.ep, P.p, P.pnp, P.pinvlo, P.hpR, X, MP, A, B, C, TT, tab, bsh, g);
+    dec_half<Lh, T>(P.mq, P.eq, P.q, P.qnp, P.qinvlo, P.hqR, X, MQ, A, B, C, TT, tab, bsh, g);
+    // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q]  (m_p < p < q)
+    if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{P.q}, Lp);
+    g_copy_param(B, P.pinvqR, Lp);
+    g_mont(C, A, B, P.q, P.qnp, Lp, TT);
+    g_mul(X, C, Lp, PArr{P.p}, Lp);
+    uint64_t c = 0;
+    for (int j = 0; j < Lh; ++j) {
+      c += (uint64_t)X[j] + (j < Lp ? MP[j] : 0u);
+      X[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    if (valid) write_tiled<T>(out, e, X, Lh, g);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ homomorphic ops
+template <int L2, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_sum(const __grid_constant__ HomParams<L2> P, size_t count,
+                                                      uint32_t* __restrict__ out) {
+  constexpr int S = L2 / T;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  RegN<S> rn;
+  if constexpr (T > 1) rn = reg_n<S, T>(P.m.n, g);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    uint32_t a[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = P.src[0][tiled_index(e, g.k * S + j, L2)];
+    for (int op = 1; op <= P.ngroups; ++op) {
+      // operands 1..ngroups-1, then the fix-up factor R^k
+      if (op < P.ngroups) {
+        const uint32_t* src = P.src[op];
+#pragma unroll
+        for (int j = 0; j < S; ++j) bsh[g.k * S + j] = src[tiled_index(e, g.k * S + j, L2)];
+      } else {
+#pragma unroll
+        for (int j = 0; j < S; ++j) bsh[g.k * S + j] = P.rk[g.k * S + j];
+      }
+      __syncwarp();
+      if constexpr (T == 1) mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+      else mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+      __syncwarp();
+    }
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) out[tiled_index(e, g.k * S + j, L2)] = a[j];
+    }
+  }
+}
+
+template <int L2, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_scal(const __grid_constant__ HomParams<L2> P,
+                                                       const uint32_t* __restrict__ ct,
+                                                       const uint64_t* __restrict__ kvec, size_t count,
+                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch) {
+  constexpr int S = L2 / T;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  RegN<S> rn;
+  if constexpr (T > 1) rn = reg_n<S, T>(P.m.n, g);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    uint32_t a[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = ct[tiled_index(e, g.k * S + j, L2)];
+#pragma unroll
+    for (int j = 0; j < S; ++j) bsh[g.k * S + j] = P.m.r2[g.k * S + j];
+    __syncwarp();
+    if constexpr (T == 1) mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+    else mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+    __syncwarp();
+    const uint64_t k = kvec[e];
+    // digits needed by the widest exponent of the warp (uniform)
+    const uint32_t hi = __reduce_or_sync(PC2_FULL, (uint32_t)(k >> 32));
+    const uint32_t lo = __reduce_or_sync(PC2_FULL, (uint32_t)k);
+    const int bits = hi ? 64 - __clz(hi) : (lo ? 32 - __clz(lo) : 1);
+    const int nd = (bits + P.w - 1) / P.w;
+    if constexpr (T == 1) modexp_var<S, T>(a, k, P.w, nd, P.m.r1, tab, bsh, ParamN{P.m.n}, P.m.np, g);
+    else modexp_var<S, T>(a, k, P.w, nd, P.m.r1, tab, bsh, rn, P.m.np, g);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < S; ++j) bsh[g.k * S + j] = (g.k == 0 && j == 0) ? 1u : 0u;
+    __syncwarp();
+    if constexpr (T == 1) mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+    else mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+    __syncwarp();
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) out[tiled_index(e, g.k * S + j, L2)] = a[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ layout conversion
+__global__ void k_pack(const uint32_t* __restrict__ canon, size_t count, int Lc, uint32_t* __restrict__ tiled) {
+  const size_t total = count * (size_t)Lc;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = i / (size_t)Lc;
+    const int j = (int)(i % (size_t)Lc);
+    tiled[tiled_index(e, j, Lc)] = canon[i];
+  }
+}
+__global__ void k_unpack(const uint32_t* __restrict__ tiled, size_t count, int Lc, uint32_t* __restrict__ canon) {
+  const size_t total = count * (size_t)Lc;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = i / (size_t)Lc;
+    const int j = (int)(i % (size_t)Lc);
+    canon[i] = tiled[tiled_index(e, j, Lc)];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class K>
+static int occupancy_grid(K kern, size_t smem, int sms) {
+  int per = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) return -1;
+  if (per < 1) return -1;
+  return per * sms;
+}
+
+template <int Lh, int T>
+int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
+  auto kern = k_enc_crt<Lh, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  const int tabw = (1 << (w - 1)) * Lh;
+  const size_t per_group = (size_t)tabw + 8 * (size_t)(2 * Lh + 4);
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+template <int L2, int T>
+int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
+  auto kern = k_enc_pub<L2, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int tabw = (1 << (P.e.w - 1)) * L2;
+  const size_t per_group = (size_t)tabw + 4 * (size_t)(L2 + 4);
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+template <int Lh, int T>
+int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
+                   void* sctx, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
+  auto kern = k_dec_crt<Lh, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  const int tabw = (1 << (w - 1)) * Lh;
+  const size_t per_group = (size_t)tabw + 7 * (size_t)(2 * Lh + 4);
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+template <int L2, int T>
+int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
+  auto kern = k_hom_sum<L2, T>;
+  int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const size_t groups_needed = (count + (kThreads / T) - 1) / (kThreads / T);
+  if ((size_t)grid > groups_needed) grid = (int)groups_needed;
+  kern<<<grid, kThreads, smem, st>>>(P, count, out);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+template <int L2, int T>
+int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* k, size_t count, uint32_t* out,
+                    ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
+  auto kern = k_hom_scal<L2, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const size_t per_group = (size_t)(1 << P.w) * L2;
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, ct, k, count, out, scratch);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st) {
+  k_pack<<<sms * 8, 256, 0, st>>>(canon, count, Lc, tiled);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st) {
+  k_unpack<<<sms * 8, 256, 0, st>>>(tiled, count, Lc, canon);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+// Supported sizes: n of 256, 512, 1024, 2048 or 3072 bits.
+#define PC2_INST_H(Lh, T)                                                                                         \
+  template int launch_enc_crt<Lh, T>(const EncCrtParams<Lh>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
+                                     ScratchFn, void*, int*, int, cudaStream_t);                                   \
+  template int launch_dec_crt<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*,   \
+                                     int, cudaStream_t);
+#define PC2_INST_2(L2, T)                                                                                         \
+  template int launch_enc_pub<L2, T>(const EncPubParams<L2>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
+                                     ScratchFn, void*, int*, int, cudaStream_t);                                   \
+  template int launch_hom_sum<L2, T>(const HomParams<L2>&, size_t, uint32_t*, int, cudaStream_t);                  \
+  template int launch_hom_scal<L2, T>(const HomParams<L2>&, const uint32_t*, const uint64_t*, size_t, uint32_t*,   \
+                                      ScratchFn, void*, int, cudaStream_t);
+PC2_INST_H(8, 1)
+PC2_INST_H(16, 1)
+PC2_INST_H(32, 1)
+PC2_INST_H(64, 1)
+PC2_INST_H(96, 1)
+PC2_INST_2(16, 1)
+PC2_INST_2(32, 1)
+PC2_INST_2(64, 1)
+PC2_INST_2(128, 2)
+PC2_INST_2(192, 4)
+
+}  // namespace pc2

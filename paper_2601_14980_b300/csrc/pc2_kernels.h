@@ -1,0 +1,38 @@
+// pc2_kernels.h -- internal launcher declarations (host side of the kernels).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pc2.h"
+#include "pc2_params.h"
+
+namespace pc2 {
+
+constexpr int kThreads = 128;  // threads per CTA of the modexp kernels
+
+// Returns device scratch of at least `bytes` (owned by the context), or null.
+typedef uint32_t* (*ScratchFn)(void* sctx, size_t bytes);
+
+template <int Lh, int T>
+int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st);
+template <int L2, int T>
+int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st);
+template <int Lh, int T>
+int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
+                   void* sctx, int sms, cudaStream_t st);
+template <int L2, int T>
+int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st);
+template <int L2, int T>
+int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* k, size_t count, uint32_t* out,
+                    ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st);
+int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st);
+int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st);
+
+// Lanes per element for each modulus width (registers: 2 segments + modulus).
+constexpr int lanes_for(int L) { return L <= 96 ? 1 : (L <= 128 ? 2 : 4); }
+
+}  // namespace pc2

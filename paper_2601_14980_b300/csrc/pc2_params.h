@@ -1,0 +1,93 @@
+// pc2_params.h -- kernel-parameter blocks and limits shared by the host
+// launchers and the CUDA kernels of libpc2.
+//
+// Everything a kernel needs about a key travels BY VALUE in its parameter
+// block (constant bank 0), so the modulus words become immediate operands of
+// the multiply-add instructions and concurrent launches with different keys
+// never share mutable state.
+#pragma once
+#include <cstdint>
+
+namespace pc2 {
+
+constexpr int kTile = 32;          // elements per tile of the interleaved layout
+constexpr int kMaxSched = 1024;    // sliding-window steps for one exponent
+constexpr int kMaxSchedHalf = 512; // per-prime decryption exponents (p-1, q-1)
+constexpr int kMaxWin = 6;         // largest window width
+constexpr int kMaxGroups = 32;     // operands of one hom_sum launch
+
+// One Montgomery modulus N of L 32-bit limbs, R = 2^(32L).
+template <int L>
+struct ModConst {
+  uint32_t n[L];   // N, little-endian words
+  uint32_t r1[L];  // R mod N (Montgomery form of 1)
+  uint32_t r2[L];  // R^2 mod N
+  uint32_t r3[L];  // R^3 mod N
+  uint32_t np;     // -N^{-1} mod 2^32
+  uint32_t pad_[3];
+};
+
+// A fixed exponent as a left-to-right sliding-window schedule.  Step 0 loads
+// table entry idx0; every later step squares `nsq` times and, when idx >= 0,
+// multiplies by table entry idx (odd powers base^(2*idx+1)).
+// Encoding: step = (nsq << 8) | (idx + 1).
+template <int MAXS>
+struct Sched {
+  uint16_t step[MAXS];
+  int32_t nsteps;
+  int32_t w;          // window width (table of 2^(w-1) odd powers)
+  int32_t montmuls;   // Montgomery products the schedule costs (table included)
+  int32_t pad_;
+};
+
+// Public-key encryption mod n^2 (L2 = limbs of n^2).
+template <int L2>
+struct EncPubParams {
+  ModConst<L2> m;          // modulus n^2
+  Sched<kMaxSched> e;      // exponent n
+  uint32_t nwords[L2 / 2]; // n (for 1 + m*n)
+  uint64_t seed;
+  uint64_t e0;             // global index of element 0 (counter of the r draw)
+  uint32_t stream;
+  int32_t mwords;          // words per plaintext: 2 (uint64 input) or L2/2 (wide, tiled input)
+};
+
+// Key-owner encryption through CRT mod p^2 and q^2 (Lh = limbs of n = limbs of p^2).
+template <int Lh>
+struct EncCrtParams {
+  ModConst<Lh> mp, mq;       // p^2, q^2
+  Sched<kMaxSched> ep, eq;   // n mod p(p-1), n mod q(q-1)
+  uint32_t nwords[Lh];       // n
+  uint32_t p2[Lh];           // p^2 (for the recombination product)
+  uint32_t pinv2R[Lh];       // (p^-2 mod q^2) * R mod q^2
+  uint64_t seed;
+  uint64_t e0;
+  uint32_t stream;
+  int32_t mwords;
+};
+
+// CRT decryption (Lh = limbs of n; p, q have Lh/2 limbs).
+template <int Lh>
+struct DecParams {
+  ModConst<Lh> mp, mq;            // p^2, q^2
+  Sched<kMaxSchedHalf> ep, eq;    // p-1, q-1
+  uint32_t p[Lh / 2], q[Lh / 2];  // the primes
+  uint32_t pnp, qnp;              // -p^-1, -q^-1 mod 2^32
+  uint32_t hpR[Lh / 2];           // h_p * R_h mod p, h_p = (-q)^-1 mod p  (R_h = 2^(32 Lh/2))
+  uint32_t hqR[Lh / 2];           // h_q * R_h mod q, h_q = (-p)^-1 mod q
+  uint32_t pinvqR[Lh / 2];        // p^-1 * R_h mod q
+  uint32_t pinvlo[Lh / 2];        // p^-1 mod 2^(32 Lh/2)
+  uint32_t qinvlo[Lh / 2];        // q^-1 mod 2^(32 Lh/2)
+};
+
+// Ciphertext products and powers mod n^2.
+template <int L2>
+struct HomParams {
+  ModConst<L2> m;
+  uint32_t rk[L2];                     // R^k mod n^2 (fix-up after k-1 products)
+  const uint32_t* src[kMaxGroups];     // hom_sum operands (tiled arrays)
+  int32_t ngroups;
+  int32_t w;                           // window width for hom_scal
+};
+
+}  // namespace pc2

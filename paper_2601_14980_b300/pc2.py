@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libpc2 (include/pc2.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device vectors are torch tensors (int32 for 32-bit words, int64 for
+64-bit plaintexts, reinterpreted bit for bit); the library never sees torch
+types.  Importing this module raises if libpc2.so is missing -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpc2.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpc2.so not built (run python -m paper_2601_14980_b300.build): %s" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i = ctypes.c_int
+
+
+def _sig(name, args, res=_i):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_strerror = _sig("pc2_strerror", [_i], ctypes.c_char_p)
+_ctx_create = _sig("pc2_ctx_create", [_i, ctypes.POINTER(_vp)])
+_ctx_destroy = _sig("pc2_ctx_destroy", [_vp], None)
+_ctx_reserve = _sig("pc2_ctx_reserve", [_vp, _sz])
+_ctx_scratch_bytes = _sig("pc2_ctx_scratch_bytes", [_vp], _sz)
+_ctx_status = _sig("pc2_ctx_status", [_vp, _vp, ctypes.POINTER(_i)])
+_ctx_set_window = _sig("pc2_ctx_set_window", [_vp, _i])
+_keygen = _sig("pc2_keygen", [_i, _u64, ctypes.POINTER(_vp)])
+_key_from_primes = _sig("pc2_key_from_primes", [_vp, _vp, _i, ctypes.POINTER(_vp)])
+_key_public = _sig("pc2_key_public", [_vp, ctypes.POINTER(_vp)])
+_key_destroy = _sig("pc2_key_destroy", [_vp], None)
+_key_info = _sig("pc2_key_info", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
+_key_export = _sig("pc2_key_export", [_vp, _vp, _vp, _vp, _vp, _vp])
+_key_cost = _sig("pc2_key_cost", [_vp, _vp, _i, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(_i)])
+_tiled_words = _sig("pc2_tiled_words", [_sz, _i], _sz)
+_pack = _sig("pc2_pack", [_vp, _vp, _sz, _i, _vp, _vp])
+_unpack = _sig("pc2_unpack", [_vp, _vp, _sz, _i, _vp, _vp])
+_encrypt = _sig("pc2_encrypt", [_vp, _vp, _vp, _sz, _u64, _u32, _u64, _vp, _vp])
+_encrypt_wide = _sig("pc2_encrypt_wide", [_vp, _vp, _vp, _sz, _u64, _u32, _u64, _vp, _vp])
+_encrypt_public = _sig("pc2_encrypt_public", [_vp, _vp, _vp, _sz, _u64, _u32, _u64, _vp, _vp])
+_decrypt = _sig("pc2_decrypt", [_vp, _vp, _vp, _sz, _vp, _vp])
+_hom_add = _sig("pc2_hom_add", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
+_hom_sum = _sig("pc2_hom_sum", [_vp, _vp, _vp, _sz, _sz, _vp, _vp])
+_hom_scal = _sig("pc2_hom_scal", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
+
+ST_RANGE, ST_QUANT, ST_TIMEOUT = 1, 2, 4
+OP_ENCRYPT, OP_ENCRYPT_PUBLIC, OP_DECRYPT = 0, 1, 2
+
+
+class Pc2Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, _strerror(code).decode(), code))
+        self.code = code
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise Pc2Error(rc, what)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def tiled_words(count: int, limbs: int) -> int:
+    return int(_tiled_words(count, limbs))
+
+
+class Context:
+    """A library context on one CUDA device (scratch memory, status word)."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(_ctx_create(device, ctypes.byref(h)), "pc2_ctx_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            _ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, nbytes: int):
+        _check(_ctx_reserve(self.h, nbytes), "pc2_ctx_reserve")
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(_ctx_scratch_bytes(self.h))
+
+    def status(self, stream=None) -> int:
+        bits = _i()
+        _check(_ctx_status(self.h, _stream(stream), ctypes.byref(bits)), "pc2_ctx_status")
+        return bits.value
+
+    def set_window(self, w: int):
+        _check(_ctx_set_window(self.h, w), "pc2_ctx_set_window")
+
+
+def _words_of(x: int, nw: int) -> np.ndarray:
+    return np.frombuffer(int(x).to_bytes(4 * nw, "little"), dtype=np.uint32).copy()
+
+
+def _int_of(w: np.ndarray) -> int:
+    return int.from_bytes(np.ascontiguousarray(w, dtype=np.uint32).tobytes(), "little")
+
+
+class Key:
+    """A Paillier key held by the library (host)."""
+
+    def __init__(self, handle):
+        self.h = handle
+        nb, pv = _i(), _i()
+        _check(_key_info(self.h, ctypes.byref(nb), ctypes.byref(pv)), "pc2_key_info")
+        self.nbits = nb.value
+        self.has_private = bool(pv.value)
+
+    @classmethod
+    def generate(cls, nbits: int, seed: int) -> "Key":
+        h = _vp()
+        _check(_keygen(nbits, seed, ctypes.byref(h)), "pc2_keygen")
+        return cls(h)
+
+    @classmethod
+    def from_primes(cls, p: int, q: int) -> "Key":
+        nw = max((p.bit_length() + 31) // 32, (q.bit_length() + 31) // 32)
+        pa, qa = _words_of(p, nw), _words_of(q, nw)
+        h = _vp()
+        _check(_key_from_primes(pa.ctypes.data, qa.ctypes.data, nw, ctypes.byref(h)), "pc2_key_from_primes")
+        return cls(h)
+
+    def public(self) -> "Key":
+        h = _vp()
+        _check(_key_public(self.h, ctypes.byref(h)), "pc2_key_public")
+        return Key(h)
+
+    def close(self):
+        if self.h:
+            _key_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def limbs(self) -> int:
+        return self.nbits // 32
+
+    def export(self) -> dict:
+        L = self.limbs
+        n = np.zeros(L, np.uint32)
+        if not self.has_private:
+            _check(_key_export(self.h, n.ctypes.data, None, None, None, None), "pc2_key_export")
+            return {"n": _int_of(n)}
+        p, q = np.zeros(L // 2, np.uint32), np.zeros(L // 2, np.uint32)
+        lam, mu = np.zeros(L, np.uint32), np.zeros(L, np.uint32)
+        _check(_key_export(self.h, n.ctypes.data, p.ctypes.data, q.ctypes.data, lam.ctypes.data, mu.ctypes.data),
+               "pc2_key_export")
+        return {"n": _int_of(n), "p": _int_of(p), "q": _int_of(q), "lambda": _int_of(lam), "mu": _int_of(mu)}
+
+    def cost(self, ctx: Context, op: int) -> tuple[int, int]:
+        """(Montgomery products per element, their limb width) of one op."""
+        mm, lb = ctypes.c_long(), _i()
+        _check(_key_cost(ctx.h, self.h, op, ctypes.byref(mm), ctypes.byref(lb)), "pc2_key_cost")
+        return mm.value, lb.value
+
+
+# ------------------------------------------------------------------ device buffers
+def empty_tiled(count: int, limbs: int, device="cuda"):
+    import torch
+
+    return torch.empty(max(tiled_words(count, limbs), 1), dtype=torch.int32, device=device)
+
+
+def pack(ctx: Context, canon, count: int, limbs: int, out=None, stream=None):
+    out = empty_tiled(count, limbs, canon.device) if out is None else out
+    _check(_pack(ctx.h, _ptr(canon), count, limbs, _ptr(out), _stream(stream)), "pc2_pack")
+    return out
+
+
+def unpack(ctx: Context, tiled, count: int, limbs: int, out=None, stream=None):
+    import torch
+
+    out = torch.empty(max(count * limbs, 1), dtype=torch.int32, device=tiled.device) if out is None else out
+    _check(_unpack(ctx.h, _ptr(tiled), count, limbs, _ptr(out), _stream(stream)), "pc2_unpack")
+    return out
+
+
+def ints_to_tiled(ctx: Context, values: Sequence[int], limbs: int, device="cuda"):
+    """Python ints -> canonical words on the host -> device -> tiled (marshalling)."""
+    import torch
+
+    canon = np.concatenate([_words_of(v, limbs) for v in values]) if len(values) else np.zeros(1, np.uint32)
+    d = torch.from_numpy(canon.view(np.int32)).to(device)
+    return pack(ctx, d, len(values), limbs)
+
+
+def tiled_to_ints(ctx: Context, tiled, count: int, limbs: int) -> list[int]:
+    import torch
+
+    canon = unpack(ctx, tiled, count, limbs)
+    torch.cuda.synchronize()
+    w = canon.cpu().numpy().view(np.uint32)
+    return [_int_of(w[i * limbs:(i + 1) * limbs]) for i in range(count)]
+
+
+# ------------------------------------------------------------------ Paillier
+def encrypt(ctx: Context, key: Key, m, seed: int, stream_id: int, e0: int = 0, out=None, public: bool = False,
+            stream=None):
+    """Eq. (itq1) on `m` (int64 tensor of uint64 plaintexts).  Returns tiled ciphertexts."""
+    count = int(m.numel())
+    out = empty_tiled(count, 2 * key.limbs, m.device) if out is None else out
+    fn = _encrypt_public if public else _encrypt
+    _check(fn(ctx.h, key.h, _ptr(m), count, seed, stream_id, e0, _ptr(out), _stream(stream)), "pc2_encrypt")
+    return out
+
+
+def encrypt_wide(ctx: Context, key: Key, m_tiled, count: int, seed: int, stream_id: int, e0: int = 0, out=None,
+                 stream=None):
+    out = empty_tiled(count, 2 * key.limbs, m_tiled.device) if out is None else out
+    _check(_encrypt_wide(ctx.h, key.h, _ptr(m_tiled), count, seed, stream_id, e0, _ptr(out), _stream(stream)),
+           "pc2_encrypt_wide")
+    return out
+
+
+def decrypt(ctx: Context, key: Key, ct, count: int, out=None, stream=None):
+    """Sec. III-C decryption; returns tiled plaintexts of key.limbs words."""
+    out = empty_tiled(count, key.limbs, ct.device) if out is None else out
+    _check(_decrypt(ctx.h, key.h, _ptr(ct), count, _ptr(out), _stream(stream)), "pc2_decrypt")
+    return out
+
+
+def hom_add(ctx: Context, key: Key, a, b, count: int, out=None, stream=None):
+    out = empty_tiled(count, 2 * key.limbs, a.device) if out is None else out
+    _check(_hom_add(ctx.h, key.h, _ptr(a), _ptr(b), count, _ptr(out), _stream(stream)), "pc2_hom_add")
+    return out
+
+
+def hom_sum(ctx: Context, key: Key, ct_groups, groups: int, count: int, out=None, stream=None):
+    out = empty_tiled(count, 2 * key.limbs, ct_groups.device) if out is None else out
+    _check(_hom_sum(ctx.h, key.h, _ptr(ct_groups), groups, count, _ptr(out), _stream(stream)), "pc2_hom_sum")
+    return out
+
+
+def hom_scal(ctx: Context, key: Key, ct, k, count: int, out=None, stream=None):
+    out = empty_tiled(count, 2 * key.limbs, ct.device) if out is None else out
+    _check(_hom_scal(ctx.h, key.h, _ptr(ct), _ptr(k), count, _ptr(out), _stream(stream)), "pc2_hom_scal")
+    return out

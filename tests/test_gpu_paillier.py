@@ -1,0 +1,141 @@
+"""GPU parity of the Paillier kernels against the CPU oracle (bit-exact).
+
+Inputs are seeded (paper_2601_14980_b300.workloads); both sides draw r from
+the same published Philox4x32-10 definition, implemented independently.
+Sizes span several 32-element tiles with a ragged tail; the full-size
+2048-bit workload (2^20 plaintexts) is checked on sampled elements."""
+import numpy as np
+import pytest
+
+from oracle import paillier as O
+from paper_2601_14980_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SEED, STREAM = 0x5EED5EED, 7
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    ctx = pc2.Context(0)
+    return torch, pc2, ctx
+
+
+def _keys(pc2, nbits, seed=1):
+    p, q = W.primes(nbits, seed)
+    return pc2.Key.from_primes(p, q), O.derive_key(p, q)
+
+
+def _oracle_ct(ko, m, e0=0, seed=SEED, stream=STREAM):
+    return O.encrypt(ko, [int(x) for x in m], [O.r_of(ko, seed, stream, e0 + e) for e in range(len(m))])
+
+
+@pytest.mark.parametrize("nbits,count", [(256, 77), (512, 70), (1024, 40)])
+def test_encrypt_crt_and_public_bit_exact(env, nbits, count):
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, nbits)
+    m = W.plaintexts_u64(count, seed=nbits)
+    m[0], m[1] = 0, np.uint64(2**64 - 1)
+    dm = torch.from_numpy(m.view(np.int64)).cuda()
+    ref = _oracle_ct(ko, m, e0=5)
+    ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM, e0=5)
+    assert pc2.tiled_to_ints(ctx, ct, count, 2 * kg.limbs) == ref
+    ctp = pc2.encrypt(ctx, kg, dm, SEED, STREAM, e0=5, public=True)
+    assert pc2.tiled_to_ints(ctx, ctp, count, 2 * kg.limbs) == ref
+    kpub = kg.public()
+    ctq = pc2.encrypt(ctx, kpub, dm, SEED, STREAM, e0=5)
+    assert pc2.tiled_to_ints(ctx, ctq, count, 2 * kg.limbs) == ref
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("nbits,count", [(256, 65), (512, 33), (1024, 40)])
+def test_decrypt_bit_exact(env, nbits, count):
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, nbits, seed=2)
+    # full-width plaintexts in [0, n), encrypted by the oracle
+    m = W.uniform_below(ko.n, count, 3) + [0, 1, ko.n - 1]
+    cnt = len(m)
+    c = O.encrypt(ko, m, [O.r_of(ko, 9, 1, e) for e in range(cnt)])
+    dct = pc2.ints_to_tiled(ctx, c, 2 * kg.limbs)
+    dm = pc2.decrypt(ctx, kg, dct, cnt)
+    assert pc2.tiled_to_ints(ctx, dm, cnt, kg.limbs) == m
+    with pytest.raises(pc2.Pc2Error):
+        pc2.decrypt(ctx, kg.public(), dct, cnt)
+
+
+def test_encrypt_wide_and_range_flag(env):
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, 512, seed=3)
+    m = W.uniform_below(ko.n, 45, 4) + [ko.n - 1]
+    dmw = pc2.ints_to_tiled(ctx, m, kg.limbs)
+    ct = pc2.encrypt_wide(ctx, kg, dmw, len(m), SEED, STREAM)
+    assert pc2.tiled_to_ints(ctx, ct, len(m), 2 * kg.limbs) == _oracle_ct(ko, m)
+    assert ctx.status() == 0
+    bad = pc2.ints_to_tiled(ctx, [ko.n], kg.limbs)
+    pc2.encrypt_wide(ctx, kg, bad, 1, SEED, STREAM)
+    assert ctx.status() & pc2.ST_RANGE
+
+
+@pytest.mark.parametrize("nbits", [256, 1024])
+def test_hom_add_sum_scal(env, nbits):
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, nbits, seed=4)
+    cnt = 37
+    groups = [O.encrypt(ko, W.uniform_below(ko.n, cnt, 10 + g), [O.r_of(ko, 3, g, e) for e in range(cnt)])
+              for g in range(35)]
+    L2 = 2 * kg.limbs
+    dg = [pc2.ints_to_tiled(ctx, grp, L2) for grp in groups]
+    out = pc2.hom_add(ctx, kg, dg[0], dg[1], cnt)
+    assert pc2.tiled_to_ints(ctx, out, cnt, L2) == O.hom_add(ko, groups[0], groups[1])
+    for G in (1, 3, 35):   # 35 > 32 operands: chained launches
+        stacked = torch.cat(dg[:G])
+        out = pc2.hom_sum(ctx, kg, stacked, G, cnt)
+        assert pc2.tiled_to_ints(ctx, out, cnt, L2) == O.hom_sum(ko, groups[:G]), G
+    k = np.array([0, 1, 2, 3, 2**64 - 1] + W.uniform_below(2**40, cnt - 5, 5), dtype=np.uint64)
+    dk = torch.from_numpy(k.view(np.int64)).cuda()
+    out = pc2.hom_scal(ctx, kg, dg[0], dk, cnt)
+    assert pc2.tiled_to_ints(ctx, out, cnt, L2) == O.hom_scal(ko, groups[0], [int(x) for x in k])
+
+
+def test_empty_and_single(env):
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, 256, seed=5)
+    dm = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = pc2.empty_tiled(1, 2 * kg.limbs)
+    assert pc2._encrypt(ctx.h, kg.h, dm.data_ptr(), 0, 1, 1, 0, out.data_ptr(), None) == 0
+    ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM)
+    assert pc2.tiled_to_ints(ctx, ct, 1, 2 * kg.limbs) == _oracle_ct(ko, [0])
+
+
+def test_full_size_2048_sampled(env):
+    """2^20 plaintexts at 2048-bit n (the benchmark's launch configuration):
+    encrypt, aggregate 16 groups of 2^16, decrypt; check sampled elements."""
+    torch, pc2, ctx = env
+    kg = pc2.Key.generate(2048, 2026)
+    e = kg.export()
+    ko = O.derive_key(e["p"], e["q"])
+    N, G = 1 << 20, 16
+    m = W.plaintexts_u64(N, seed=7)
+    dm = torch.from_numpy(m.view(np.int64)).cuda()
+    L2 = 2 * kg.limbs
+    ct = torch.empty(G * pc2.tiled_words(N // G, L2), dtype=torch.int32, device="cuda")
+    for g in range(G):   # group g = elements [g N/G, (g+1) N/G), r counters continue across groups
+        seg = ct[g * pc2.tiled_words(N // G, L2):(g + 1) * pc2.tiled_words(N // G, L2)]
+        pc2.encrypt(ctx, kg, dm[g * (N // G):(g + 1) * (N // G)], SEED, STREAM, e0=g * (N // G), out=seg)
+    agg = pc2.hom_sum(ctx, kg, ct, G, N // G)
+    dec = pc2.decrypt(ctx, kg, agg, N // G)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    idx = sorted(set([0, N // G - 1] + rng.integers(0, N // G, 6).tolist()))
+    canon = pc2.unpack(ctx, ct[: pc2.tiled_words(N // G, L2)], N // G, L2).cpu().numpy().view(np.uint32)
+    ref = _oracle_ct(ko, [m[i] for i in idx[:3]], e0=0)
+    for j, i in enumerate(idx[:3]):
+        assert int.from_bytes(canon[i * L2:(i + 1) * L2].tobytes(), "little") == ref[j]
+    decw = pc2.unpack(ctx, dec, N // G, kg.limbs).cpu().numpy().view(np.uint32)
+    for i in idx:
+        expect = sum(int(m[g * (N // G) + i]) for g in range(G)) % ko.n
+        assert int.from_bytes(decw[i * kg.limbs:(i + 1) * kg.limbs].tobytes(), "little") == expect
