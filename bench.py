@@ -1,0 +1,297 @@
+"""Benchmark of the Paillier hot path of 3P-ADMM-PC2 on B300.
+
+Workload (one step): 2048-bit n, 2^20 quantized plaintexts rint(x 2^24) + 2^47
+(x ~ N(0,1)); encrypt all of them (key-owner CRT path), aggregate the 16 node
+groups of 2^16 by ciphertext products mod n^2, CRT-decrypt the 2^16
+aggregates.  Metric: Paillier encryptions + decryptions per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank on its own 2^20
+plaintexts (weak scaling, no data-path collective).  --impl reference times
+the CPU oracle (oracle/) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NBITS = 2048
+N_PLAIN = 1 << 20
+GROUPS = 16
+SEED, STREAM = 0xB300, 1
+METRIC = "Paillier enc/dec per s @2048-bit"
+UNIT = "Paillier enc+dec ops/s"
+WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
+IMAD_PER_CLK_SM = 64   # 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _oracle_sample(args):
+    """One bounded oracle step: encrypt `per_group` plaintexts in each of 16
+    groups, aggregate, decrypt the aggregates.  Runs in a worker process."""
+    p, q, m_list, e_list, seed, stream = args
+    from oracle import paillier as O
+
+    ko = O.derive_key(p, q)
+    c = O.encrypt(ko, m_list, [O.r_of(ko, seed, stream, e) for e in e_list])
+    return c
+
+
+def _cpu_reference(steps: int, warmup: int, per_group: int = 4):
+    """Time the oracle (as it stands) on the host cores: each step encrypts
+    16 x per_group plaintexts, multiplies the 16 groups, decrypts per_group
+    aggregates.  Returns (ops/s, cores, sample description, seconds/step)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from oracle import paillier as O
+    from paper_2601_14980_b300 import workloads as W
+
+    p, q = W.primes(NBITS, 2026)
+    ko = O.derive_key(p, q)
+    m = W.plaintexts_u64(GROUPS * per_group, seed=7)
+    cores = os.cpu_count() or 1
+    work = [(p, q, [int(m[g * per_group + i])], [g * (N_PLAIN // GROUPS) + i], SEED, STREAM)
+            for g in range(GROUPS) for i in range(per_group)]
+    times = []
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_sample, work[:cores]))  # start the workers
+        for s in range(warmup + steps):
+            t0 = time.perf_counter()
+            cts = [r[0] for r in ex.map(_oracle_sample, work)]
+            groups = [cts[g * per_group:(g + 1) * per_group] for g in range(GROUPS)]
+            agg = O.hom_sum(ko, groups)
+            dec = list(ex.map(_dec_worker, [(p, q, a) for a in agg]))
+            t1 = time.perf_counter()
+            if s >= warmup:
+                times.append(t1 - t0)
+    per = statistics.mean(times)
+    ops = GROUPS * per_group + per_group
+    sample = "%d encryptions + %d-group products + %d decryptions per step (of the 2^20 workload), process pool" % (
+        GROUPS * per_group, GROUPS, per_group)
+    return ops / per, cores, sample, per
+
+
+def _dec_worker(args):
+    p, q, c = args
+    from oracle import paillier as O
+
+    return O.decrypt(O.derive_key(p, q), [c])[0]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+    from paper_2601_14980_b300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, per = _cpu_reference(steps=1, warmup=0)
+        cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    ctx = pc2.Context(dev)
+    key = pc2.Key.generate(NBITS, 2026)
+    L2 = 2 * key.limbs
+    per_group = N_PLAIN // GROUPS
+    m_host = W.plaintexts_u64(N_PLAIN, seed=7 + rank)
+    m_pinned = torch.from_numpy(m_host.view(np.int64)).pin_memory()
+    dm = m_pinned.to(f"cuda:{dev}")
+    ct = torch.empty(pc2.tiled_words(N_PLAIN, L2), dtype=torch.int32, device=dev)
+    agg = torch.empty(pc2.tiled_words(per_group, L2), dtype=torch.int32, device=dev)
+    dec = torch.empty(pc2.tiled_words(per_group, key.limbs), dtype=torch.int32, device=dev)
+    dec_host = torch.empty(dec.numel(), dtype=torch.int32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+    st = torch.cuda.current_stream()
+    e0 = rank * N_PLAIN
+
+    def step(ev=None, e2e=False):
+        if e2e:
+            dm.copy_(m_pinned, non_blocking=True)
+        if ev: ev[0].record(st)
+        pc2.encrypt(ctx, key, dm, SEED, STREAM, e0=e0, out=ct)
+        if ev: ev[1].record(st)
+        pc2.hom_sum(ctx, key, ct, GROUPS, per_group, out=agg)
+        if ev: ev[2].record(st)
+        pc2.decrypt(ctx, key, agg, per_group, out=dec)
+        if ev: ev[3].record(st)
+        if e2e:
+            dec_host.copy_(dec, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status raised during warm-up")
+
+    clocks = Clocks(dev) if rank == 0 else None
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist: dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()
+        step(evs[s])
+    torch.cuda.synchronize()
+    if dist: dist.barrier()
+    clk = clocks.stop() if clocks else None
+    t_enc = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
+    t_sum = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
+    t_dec = [evs[s][2].elapsed_time(evs[s][3]) for s in range(args.steps)]
+    step_ms = [a + b + c for a, b, c in zip(t_enc, t_sum, t_dec)]
+    ms = statistics.mean(step_ms)
+
+    # end to end: host plaintexts in, host plaintexts out, through the C ABI
+    e2e_ms = []
+    for s in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        step(None, e2e=True)
+        b.record(st)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    ms_e2e = statistics.mean(e2e_ms)
+
+    if dist:
+        t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    ops = (N_PLAIN + per_group) * world
+    value = ops / (ms / 1e3)
+
+    # roofline of the dominant kernel (encryption): algorithmic IMADs / time
+    mm, lb = key.cost(ctx, pc2.OP_ENCRYPT)
+    imad_per_elem = mm * (4 * lb * lb + lb)
+    enc_ms = statistics.mean(t_enc)
+    achieved = imad_per_elem * N_PLAIN / (enc_ms / 1e3) / 1e12
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12
+    dmm, dlb = key.cost(ctx, pc2.OP_DECRYPT)
+    dec_ms = statistics.mean(t_dec)
+    if rank != 0:
+        if dist: dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_bits": NBITS, "plaintexts_per_gpu": N_PLAIN, "groups": GROUPS,
+                   "encrypt_path": "key-owner CRT (mod p^2, q^2)", "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "dp%d (independent shards)" % world},
+        "detail": {"encrypt_ms": enc_ms, "hom_sum_ms": statistics.mean(t_sum), "decrypt_ms": dec_ms,
+                   "enc_per_s": N_PLAIN / (enc_ms / 1e3), "dec_per_s": per_group / (dec_ms / 1e3),
+                   "enc_montmuls_per_elem": mm, "dec_montmuls_per_elem": dmm, "montmul_limbs": lb},
+        "roofline": {"bound": "alu", "kernel": "k_enc_crt", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "%d SMs x %d IMAD/clk x %.0f MHz (unit count x max SM clock)" % (sms, IMAD_PER_CLK_SM, sm_max)},
+        "e2e": {"value": ops / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(m_pinned.numel() * 8),
+                "d2h_bytes_per_step": int(dec_host.numel() * 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu_base,
+    }
+    print(json.dumps(line))
+    if dist: dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    v, cores, sample, per = _cpu_reference(steps=args.steps, warmup=args.warmup, per_group=1)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_bits": NBITS, "plaintexts_per_gpu": N_PLAIN, "groups": GROUPS},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pc2", choices=["pc2", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
