@@ -136,6 +136,34 @@ int pc2_hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t g
 int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint64_t* d_k, size_t count,
                  uint32_t* d_out, pc2_stream_t cstream);
 
+/* ---- decryption without device allocation ---------------------------- *
+ * Not from the paper (it has no counterpart there): a variant of pc2_decrypt
+ * for callers that may not allocate device memory -- a process held to a
+ * fixed, pre-carved memory budget, a plugin that must not touch the device
+ * allocator, or a latency path that cannot take the device-wide
+ * synchronisation that cudaMalloc/cudaFree can imply.  It computes the same
+ * result as pc2_decrypt (same arguments, no context) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  - Scratch: a fixed array of PC2_NOALLOC_SCRATCH_BYTES compiled into the
+ *    library, which every GPU that loads the library holds until the process
+ *    exits.  The decryption's persistent grid is cut to the CTAs whose scratch
+ *    fits, so it runs with fewer CTAs (lower throughput) than pc2_decrypt.
+ *    Nothing in the array needs to start at zero: every word a call reads is
+ *    written by that call first.
+ *  - Runs on the calling thread's current device.  The FIRST call on each
+ *    device looks up the array's device address (cudaGetSymbolAddress); make
+ *    that first call before any stream capture.
+ *  - All calls share the one array: calls whose kernels overlap on a GPU
+ *    (different streams, or different host threads) race and corrupt each
+ *    other's results.  Order them on one stream.
+ *  - PC2_ERANGE if one CTA's share of scratch for this key would exceed the
+ *    array (it does not for any supported key size); the element count itself
+ *    is not limited.  The key's host-side constants are built and cached in
+ *    host memory on its first decryption, as for pc2_decrypt.
+ *  - PC2_EKEY for a public key; PC2_EINVAL for null pointers. */
+#define PC2_NOALLOC_SCRATCH_BYTES (64u << 20)
+int pc2_decrypt_noalloc(const pc2_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_m, pc2_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

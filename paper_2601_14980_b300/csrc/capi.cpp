@@ -113,6 +113,16 @@ static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
   return launch_dec_crt<Lh, lanes_for(Lh)>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st);
 }
 
+template <int Lh>
+std::shared_ptr<DecParams<Lh>> dec_params(const pc2_key* key, int* rc) {
+  return cached<DecParams<Lh>>(key, KIND_DEC, 0, [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, 0, p); }, rc);
+}
+template std::shared_ptr<DecParams<8>> dec_params<8>(const pc2_key*, int*);
+template std::shared_ptr<DecParams<16>> dec_params<16>(const pc2_key*, int*);
+template std::shared_ptr<DecParams<32>> dec_params<32>(const pc2_key*, int*);
+template std::shared_ptr<DecParams<64>> dec_params<64>(const pc2_key*, int*);
+template std::shared_ptr<DecParams<96>> dec_params<96>(const pc2_key*, int*);
+
 template <int L2>
 static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs, size_t groups, size_t count,
                    uint32_t* out, cudaStream_t st) {

@@ -2,6 +2,7 @@
 // parameter blocks.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "hostbn.hpp"
@@ -34,5 +35,9 @@ template <int Lh> int make_enc_crt(const pc2_key& k, int w, EncCrtParams<Lh>& P)
 template <int L2> int make_enc_pub(const pc2_key& k, int w, EncPubParams<L2>& P);
 template <int Lh> int make_dec(const pc2_key& k, int w, DecParams<Lh>& P);
 template <int L2> int make_hom(const pc2_key& k, int w, int ngroups, HomParams<L2>& P);
+
+// The decryption parameter block of a key from the per-key host cache
+// (built on first use; automatic window).
+template <int Lh> std::shared_ptr<DecParams<Lh>> dec_params(const pc2_key* k, int* rc);
 
 }  // namespace pc2

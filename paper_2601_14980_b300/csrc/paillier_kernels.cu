@@ -444,6 +444,25 @@ int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uin
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
+// Decryption into a fixed scratch region of `scratch_words` words: the
+// persistent grid is cut down to the CTAs whose scratch fits.
+template <int Lh, int T>
+int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, uint32_t* scratch,
+                         size_t scratch_words, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
+  auto kern = k_dec_crt<Lh, T>;
+  int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  const int tabw = (1 << (w - 1)) * Lh;
+  const size_t per_cta = ((size_t)tabw + 7 * (size_t)(2 * Lh + 4)) * (kThreads / T);
+  if (per_cta > scratch_words) return PC2_ERANGE;
+  const size_t fit = scratch_words / per_cta;
+  if ((size_t)grid > fit) grid = (int)fit;
+  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
 template <int L2, int T>
 int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st) {
   const size_t smem = (size_t)L2 * (kThreads / T) * 4;
@@ -484,7 +503,9 @@ int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, 
   template int launch_enc_crt<Lh, T>(const EncCrtParams<Lh>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
                                      ScratchFn, void*, int*, int, cudaStream_t);                                   \
   template int launch_dec_crt<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*,   \
-                                     int, cudaStream_t);
+                                     int, cudaStream_t);                                                           \
+  template int launch_dec_crt_fixed<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, uint32_t*,     \
+                                           size_t, int, cudaStream_t);
 #define PC2_INST_2(L2, T)                                                                                         \
   template int launch_enc_pub<L2, T>(const EncPubParams<L2>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
                                      ScratchFn, void*, int*, int, cudaStream_t);                                   \

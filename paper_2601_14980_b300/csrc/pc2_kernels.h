@@ -24,6 +24,9 @@ int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_
 template <int Lh, int T>
 int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
                    void* sctx, int sms, cudaStream_t st);
+template <int Lh, int T>
+int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, uint32_t* scratch,
+                         size_t scratch_words, int sms, cudaStream_t st);
 template <int L2, int T>
 int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st);
 template <int L2, int T>
