@@ -156,6 +156,8 @@ def run_gpu(args):
         v, cores, sample, per = _cpu_reference(steps=1, warmup=0)
         cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
+    global N_PLAIN, GROUPS
+    N_PLAIN, GROUPS = args.plaintexts, args.groups
     ctx = pc2.Context(dev)
     key = pc2.Key.generate(NBITS, 2026)
     L2 = 2 * key.limbs
@@ -286,6 +288,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pc2", choices=["pc2", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
+    ap.add_argument("--groups", type=int, default=GROUPS)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

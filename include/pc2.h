@@ -136,6 +136,66 @@ int pc2_hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t g
 int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint64_t* d_k, size_t count,
                  uint32_t* d_out, pc2_stream_t cstream);
 
+/* ---- quantizer ------------------------------------------------------- *
+ * Eq. (et21) with one public range [zmin, zmax] and scale S = 2^log2_scale
+ * (Delta = S (zmax - zmin)): gamma 2 -> q = rint((u - zmin) S) in [0, Delta];
+ * gamma 1 -> q = rint((u - zmin) S^2) in [0, Delta S]; negate = 1 quantizes -u.
+ * IEEE double, round half to even, no contraction.  Out-of-range inputs are
+ * clamped and raise PC2_ST_QUANT.  d_u: n doubles; d_q: n uint64. */
+int pc2_quantize(pc2_ctx* ctx, const double* d_u, size_t n, double zmin, double zmax, int log2_scale, int gamma,
+                 int negate, uint64_t* d_q, pc2_stream_t stream);
+
+/* ---- 3P-ADMM-PC2 on one GPU (Algorithm 1) ------------------------------- *
+ * The K edge nodes are segments of device vectors (node k owns elements
+ * [N_0 + ... + N_{k-1}, ... + N_k)).  Inputs are the edge nodes' set-up
+ * results of Sec. II: d_alpha = alpha_k = B_k A_k^T y (N doubles, node by node)
+ * and d_Bbar = rho B_k, B_k = (A_k^T A_k + rho I)^-1 (sum N_k^2 doubles,
+ * row-major per node, node by node).  pc2_admm_create quantizes them
+ * (Gamma1(alpha), Gamma2(Bbar)), encrypts alpha (r-stream 0) and sets
+ * x = z = v = 0, round 1.  One private round (pc2_admm_round):
+ *   Gamma2(z), Gamma2(-v); z-hat, (-v)-hat = E(.) with r-streams
+ *   (t << 8) | 1 and (t << 8) | 2 (t = round); s-hat = z-hat (+) (-v)-hat;
+ *   x-hat_k = alpha-hat_k (+) Gamma2(Bbar_k) (x) s-hat_k (Eq. (itq2));
+ *   D = decrypt(x-hat); x = exact decode of D; z = S_{lambda/rho}(v + x);
+ *   v = v + x - z (Eqs. (ty32), (u78)).
+ * The exact decode: with mS = zmin S (must be an integer),
+ *   x_i = fl(D_i + mS S + 2 mS sum_j b_ij + mS sum_j a_j + 2 mS^2 N_k) / S^2,
+ * a_j = Gamma2(z_j) + Gamma2(-v_j), b = Gamma2(Bbar_k): the float64 rounding
+ * of alpha~ + Bbar~ w~ on the dequantized inputs (Theorem 1 written out).
+ * The batched path (per_node = 0) runs all nodes in the same launches and
+ * replays rounds 2.. as one CUDA graph; per_node = 1 launches each node's
+ * encryption, aggregation, matvec and decryption separately. */
+typedef struct {
+  int nodes;             /* K */
+  const int* node_sizes; /* host array of K sizes N_k */
+  double lambda, rho;
+  double zmin, zmax;     /* public quantization range */
+  int log2_scale;        /* S = 2^log2_scale */
+  uint64_t seed;         /* Philox key of the encryption randomness */
+  int per_node;          /* 0: batched + CUDA graph; 1: one launch per node */
+} pc2_admm_params;
+
+typedef struct pc2_admm pc2_admm;
+int pc2_admm_create(pc2_ctx* ctx, const pc2_key* key, const pc2_admm_params* params, const double* d_alpha,
+                    const double* d_Bbar, pc2_admm** out, pc2_stream_t stream);
+void pc2_admm_destroy(pc2_admm* admm);
+/* x = z = v = 0, round counter 1 (synchronises `stream`). */
+int pc2_admm_reset(pc2_admm* admm, pc2_stream_t stream);
+/* `rounds` private rounds of Algorithm 1. */
+int pc2_admm_round(pc2_admm* admm, int rounds, pc2_stream_t stream);
+/* `rounds` plaintext Dis-ADMM rounds (Eq. (sldo091), (ty32), (u78)) on the same state, FP64. */
+int pc2_admm_round_plain(pc2_admm* admm, int rounds, pc2_stream_t stream);
+/* Copies x, z, v (device, N doubles each; any may be NULL) and the next round number (host; synchronises). */
+int pc2_admm_get(pc2_admm* admm, double* d_x, double* d_z, double* d_v, uint32_t* h_round, pc2_stream_t stream);
+/* Restores a checkpoint: x, z, v and the next round number (>= 1). */
+int pc2_admm_set(pc2_admm* admm, const double* d_x, const double* d_z, const double* d_v, uint32_t round,
+                 pc2_stream_t stream);
+/* Device pointers of the last round's ciphertexts (tiled) and decrypted integers, and N. */
+int pc2_admm_buffers(pc2_admm* admm, const uint32_t** zhat, const uint32_t** vhat, const uint32_t** xhat,
+                     const uint32_t** alpha_hat, const uint32_t** D, int* N);
+/* Bucket window c, windows per exponent, CTA row tiles of the matvec. */
+int pc2_admm_info(const pc2_admm* admm, int* c, int* nwin, int* ntiles);
+
 /* ---- decryption without device allocation ---------------------------- *
  * Not from the paper (it has no counterpart there): a variant of pc2_decrypt
  * for callers that may not allocate device memory -- a process held to a

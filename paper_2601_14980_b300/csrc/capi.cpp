@@ -16,14 +16,7 @@
 #include "philox.h"
 #include "pc2_kernels.h"
 
-struct pc2_ctx {
-  int device = 0;
-  int sms = 0;
-  uint32_t* scratch = nullptr;
-  size_t scratch_bytes = 0;
-  int* status = nullptr;  // device word of PC2_ST_* bits
-  int window = 0;         // 0 = automatic
-};
+#include "ctx.hpp"
 
 namespace pc2 {
 
@@ -72,6 +65,8 @@ static uint32_t* ctx_scratch(void* c, size_t bytes) {
   return ctx->scratch;
 }
 
+uint32_t* ctx_scratch_get(pc2_ctx* ctx, size_t bytes) { return ctx_scratch(ctx, bytes); }
+
 template <int Lh>
 static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
                    uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
@@ -86,6 +81,40 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->e0 = e0;
   P->mwords = mw ? Lh : 2;
   return launch_enc_crt<Lh, lanes_for(Lh)>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+}
+
+template <int Lh>
+static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, size_t count, uint64_t seed,
+                         const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* out, cudaStream_t st,
+                         size_t base) {
+  int rc;
+  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, ctx->window,
+                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, ctx->window, P); }, &rc);
+  if (!P0) return rc;
+  std::unique_ptr<EncCrtParams<Lh>> P(new (std::nothrow) EncCrtParams<Lh>(*P0));
+  if (!P) return PC2_ENOMEM;
+  P->seed = seed;
+  P->e0 = e0;
+  P->mwords = 2;
+  P->round_ptr = round_ptr;
+  P->kind = kind;
+  return launch_enc_crt<Lh, lanes_for(Lh)>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st,
+                                           base);
+}
+
+int encrypt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
+                  const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* d_ct, cudaStream_t st,
+                  size_t base) {
+  if (!ctx || !key || !key->priv) return PC2_EKEY;
+  if (!count) return PC2_OK;
+  switch (key->Lh) {
+    case 8: return enc_crt_round<8>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    case 16: return enc_crt_round<16>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    case 32: return enc_crt_round<32>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    case 64: return enc_crt_round<64>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    case 96: return enc_crt_round<96>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    default: return PC2_EUNSUPPORTED;
+  }
 }
 
 template <int L2>
@@ -105,12 +134,13 @@ static int enc_pub(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
 }
 
 template <int Lh>
-static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st) {
+static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
+               size_t base = 0) {
   int rc;
   auto P = cached<DecParams<Lh>>(key, KIND_DEC, ctx->window,
                                  [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, ctx->window, p); }, &rc);
   if (!P) return rc;
-  return launch_dec_crt<Lh, lanes_for(Lh)>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st);
+  return launch_dec_crt<Lh, lanes_for(Lh)>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
 }
 
 template <int Lh>
@@ -125,7 +155,7 @@ template std::shared_ptr<DecParams<96>> dec_params<96>(const pc2_key*, int*);
 
 template <int L2>
 static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs, size_t groups, size_t count,
-                   uint32_t* out, cudaStream_t st) {
+                   uint32_t* out, cudaStream_t st, size_t base = 0) {
   // chunks of at most kMaxGroups operands; later chunks start from the running product
   size_t done = 0;
   bool first = true;
@@ -139,11 +169,39 @@ static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs
     int rc = make_hom<L2>(*key, ctx->window, k, *P);
     if (rc) return rc;
     for (int i = 0; i < k; ++i) P->src[i] = ops[i];
-    rc = launch_hom_sum<L2, lanes_for(L2)>(*P, count, out, ctx->sms, st);
+    rc = launch_hom_sum<L2, lanes_for(L2)>(*P, count, out, ctx->sms, st, base);
     if (rc) return rc;
     first = false;
   }
   return PC2_OK;
+}
+
+int hom_add_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* a, const uint32_t* b, size_t count, uint32_t* out,
+               cudaStream_t st, size_t base) {
+  if (!count) return PC2_OK;
+  const uint32_t* srcs[2] = {a, b};
+  switch (key->Lh) {
+    case 8: return hom_sum<16>(ctx, key, srcs, 2, count, out, st, base);
+    case 16: return hom_sum<32>(ctx, key, srcs, 2, count, out, st, base);
+    case 32: return hom_sum<64>(ctx, key, srcs, 2, count, out, st, base);
+    case 64: return hom_sum<128>(ctx, key, srcs, 2, count, out, st, base);
+    case 96: return hom_sum<192>(ctx, key, srcs, 2, count, out, st, base);
+    default: return PC2_EUNSUPPORTED;
+  }
+}
+
+int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
+               size_t base) {
+  if (!key->priv) return PC2_EKEY;
+  if (!count) return PC2_OK;
+  switch (key->Lh) {
+    case 8: return dec<8>(ctx, key, ct, count, out, st, base);
+    case 16: return dec<16>(ctx, key, ct, count, out, st, base);
+    case 32: return dec<32>(ctx, key, ct, count, out, st, base);
+    case 64: return dec<64>(ctx, key, ct, count, out, st, base);
+    case 96: return dec<96>(ctx, key, ct, count, out, st, base);
+    default: return PC2_EUNSUPPORTED;
+  }
 }
 
 template <int L2>

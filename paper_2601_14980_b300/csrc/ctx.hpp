@@ -1,0 +1,36 @@
+// ctx.hpp -- the library context (internal layout) and internal helpers
+// shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pc2.h"
+
+struct pc2_ctx {
+  int device = 0;
+  int sms = 0;
+  uint32_t* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int* status = nullptr;  // device word of PC2_ST_* bits
+  int window = 0;         // 0 = automatic
+};
+
+namespace pc2 {
+
+// Scratch of at least `bytes` from the context (grows it outside stream capture).
+uint32_t* ctx_scratch_get(pc2_ctx* ctx, size_t bytes);
+
+// Key-owner encryption whose r-stream id is read on the device:
+// (*round_ptr << 8) | kind (see EncCrtParams).
+// `base`: position of element 0 of this call inside the tiled arrays.
+int encrypt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
+                  const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* d_ct, cudaStream_t st,
+                  size_t base = 0);
+int hom_add_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* a, const uint32_t* b, size_t count, uint32_t* out,
+               cudaStream_t st, size_t base);
+int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
+               size_t base);
+
+}  // namespace pc2

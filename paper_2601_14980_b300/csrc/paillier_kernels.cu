@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const _
                                                       const uint64_t* __restrict__ m64,
                                                       const uint32_t* __restrict__ mwide, size_t count,
                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
-                                                      int tabw, int* status) {
+                                                      int tabw, int* status, size_t base_out) {
   extern __shared__ uint32_t bsh_all[];
   const Grp<T> g;
   const Layout ly(T);
@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const _
     size_t e = base + ly.gl;
     const bool valid = e < count;
     if (!valid) e = count - 1;
-    gen_r(X, P.seed, P.stream, P.e0 + e, Lh + 2, 2 * Lh);
+    const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | P.kind) : P.stream;
+    gen_r(X, P.seed, sid, P.e0 + e, Lh + 2, 2 * Lh);
     make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid, status);
     enc_half<Lh, T>(P.mp, P.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
     enc_half<Lh, T>(P.mq, P.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const _
       X[j] = (uint32_t)c;
       c >>= 32;
     }
-    if (valid) write_tiled<T>(out, e, X, 2 * Lh, g);
+    if (valid) write_tiled<T>(out, base_out + e, X, 2 * Lh, g);
     __syncwarp();
   }
 }
@@ -246,7 +247,7 @@ template <int Lh, int T>
 __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const __grid_constant__ DecParams<Lh> P,
                                                       const uint32_t* __restrict__ ct, size_t count,
                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
-                                                      int tabw) {
+                                                      int tabw, size_t ebase) {
   constexpr int Lp = Lh / 2;
   extern __shared__ uint32_t bsh_all[];
   const Grp<T> g;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
     size_t e = base + ly.gl;
     const bool valid = e < count;
     if (!valid) e = count - 1;
-    for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(e, j, 2 * Lh)];
+    for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(ebase + e, j, 2 * Lh)];
     dec_half<Lh, T>(P.mp, P.ep, P.p, P.pnp, P.pinvlo, P.hpR, X, MP, A, B, C, TT, tab, bsh, g);
     dec_half<Lh, T>(P.mq, P.eq, P.q, P.qnp, P.qinvlo, P.hqR, X, MQ, A, B, C, TT, tab, bsh, g);
     // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q]  (m_p < p < q)
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
       X[j] = (uint32_t)c;
       c >>= 32;
     }
-    if (valid) write_tiled<T>(out, e, X, Lh, g);
+    if (valid) write_tiled<T>(out, ebase + e, X, Lh, g);
     __syncwarp();
   }
 }
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
 // ------------------------------------------------------------------ homomorphic ops
 template <int L2, int T>
 __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_sum(const __grid_constant__ HomParams<L2> P, size_t count,
-                                                      uint32_t* __restrict__ out) {
+                                                      uint32_t* __restrict__ out, size_t ebase) {
   constexpr int S = L2 / T;
   extern __shared__ uint32_t bsh_all[];
   const Grp<T> g;
@@ -298,13 +299,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_sum(const _
     if (!valid) e = count - 1;
     uint32_t a[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j) a[j] = P.src[0][tiled_index(e, g.k * S + j, L2)];
+    for (int j = 0; j < S; ++j) a[j] = P.src[0][tiled_index(ebase + e, g.k * S + j, L2)];
     for (int op = 1; op <= P.ngroups; ++op) {
       // operands 1..ngroups-1, then the fix-up factor R^k
       if (op < P.ngroups) {
         const uint32_t* src = P.src[op];
 #pragma unroll
-        for (int j = 0; j < S; ++j) bsh[g.k * S + j] = src[tiled_index(e, g.k * S + j, L2)];
+        for (int j = 0; j < S; ++j) bsh[g.k * S + j] = src[tiled_index(ebase + e, g.k * S + j, L2)];
       } else {
 #pragma unroll
         for (int j = 0; j < S; ++j) bsh[g.k * S + j] = P.rk[g.k * S + j];
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_sum(const _
     }
     if (valid) {
 #pragma unroll
-      for (int j = 0; j < S; ++j) out[tiled_index(e, g.k * S + j, L2)] = a[j];
+      for (int j = 0; j < S; ++j) out[tiled_index(ebase + e, g.k * S + j, L2)] = a[j];
     }
   }
 }
@@ -399,7 +400,7 @@ static int occupancy_grid(K kern, size_t smem, int sms) {
 
 template <int Lh, int T>
 int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
-                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st) {
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base) {
   const size_t smem = (size_t)Lh * (kThreads / T) * 4;
   auto kern = k_enc_crt<Lh, T>;
   const int grid = occupancy_grid(kern, smem, sms);
@@ -409,7 +410,7 @@ int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_
   const size_t per_group = (size_t)tabw + 8 * (size_t)(2 * Lh + 4);
   uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
   if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status);
+  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status, base);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
@@ -430,7 +431,7 @@ int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_
 
 template <int Lh, int T>
 int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
-                   void* sctx, int sms, cudaStream_t st) {
+                   void* sctx, int sms, cudaStream_t st, size_t base) {
   const size_t smem = (size_t)Lh * (kThreads / T) * 4;
   auto kern = k_dec_crt<Lh, T>;
   const int grid = occupancy_grid(kern, smem, sms);
@@ -440,7 +441,7 @@ int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uin
   const size_t per_group = (size_t)tabw + 7 * (size_t)(2 * Lh + 4);
   uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
   if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw);
+  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw, base);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
@@ -459,19 +460,19 @@ int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t coun
   if (per_cta > scratch_words) return PC2_ERANGE;
   const size_t fit = scratch_words / per_cta;
   if ((size_t)grid > fit) grid = (int)fit;
-  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw);
+  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw, (size_t)0);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
 template <int L2, int T>
-int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st) {
+int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st, size_t base) {
   const size_t smem = (size_t)L2 * (kThreads / T) * 4;
   auto kern = k_hom_sum<L2, T>;
   int grid = occupancy_grid(kern, smem, sms);
   if (grid < 0) return PC2_ECUDA;
   const size_t groups_needed = (count + (kThreads / T) - 1) / (kThreads / T);
   if ((size_t)grid > groups_needed) grid = (int)groups_needed;
-  kern<<<grid, kThreads, smem, st>>>(P, count, out);
+  kern<<<grid, kThreads, smem, st>>>(P, count, out, base);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
@@ -501,15 +502,15 @@ int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, 
 // Supported sizes: n of 256, 512, 1024, 2048 or 3072 bits.
 #define PC2_INST_H(Lh, T)                                                                                         \
   template int launch_enc_crt<Lh, T>(const EncCrtParams<Lh>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
-                                     ScratchFn, void*, int*, int, cudaStream_t);                                   \
+                                     ScratchFn, void*, int*, int, cudaStream_t, size_t);                           \
   template int launch_dec_crt<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*,   \
-                                     int, cudaStream_t);                                                           \
+                                     int, cudaStream_t, size_t);                                                   \
   template int launch_dec_crt_fixed<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, uint32_t*,     \
                                            size_t, int, cudaStream_t);
 #define PC2_INST_2(L2, T)                                                                                         \
   template int launch_enc_pub<L2, T>(const EncPubParams<L2>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
                                      ScratchFn, void*, int*, int, cudaStream_t);                                   \
-  template int launch_hom_sum<L2, T>(const HomParams<L2>&, size_t, uint32_t*, int, cudaStream_t);                  \
+  template int launch_hom_sum<L2, T>(const HomParams<L2>&, size_t, uint32_t*, int, cudaStream_t, size_t);          \
   template int launch_hom_scal<L2, T>(const HomParams<L2>&, const uint32_t*, const uint64_t*, size_t, uint32_t*,   \
                                       ScratchFn, void*, int, cudaStream_t);
 PC2_INST_H(8, 1)

@@ -17,18 +17,18 @@ typedef uint32_t* (*ScratchFn)(void* sctx, size_t bytes);
 
 template <int Lh, int T>
 int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
-                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st);
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base = 0);
 template <int L2, int T>
 int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
                    ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st);
 template <int Lh, int T>
 int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
-                   void* sctx, int sms, cudaStream_t st);
+                   void* sctx, int sms, cudaStream_t st, size_t base = 0);
 template <int Lh, int T>
 int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, uint32_t* scratch,
                          size_t scratch_words, int sms, cudaStream_t st);
 template <int L2, int T>
-int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st);
+int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st, size_t base = 0);
 template <int L2, int T>
 int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* k, size_t count, uint32_t* out,
                     ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st);

@@ -53,6 +53,8 @@ struct EncPubParams {
 };
 
 // Key-owner encryption through CRT mod p^2 and q^2 (Lh = limbs of n = limbs of p^2).
+// When round_ptr is set the r-stream id is (*round_ptr << 8) | kind, read on
+// the device (so a captured ADMM round can be replayed round after round).
 template <int Lh>
 struct EncCrtParams {
   ModConst<Lh> mp, mq;       // p^2, q^2
@@ -64,6 +66,9 @@ struct EncCrtParams {
   uint64_t e0;
   uint32_t stream;
   int32_t mwords;
+  const uint32_t* round_ptr;
+  uint32_t kind;
+  uint32_t pad_;
 };
 
 // CRT decryption (Lh = limbs of n; p, q have Lh/2 limbs).
@@ -88,6 +93,17 @@ struct HomParams {
   const uint32_t* src[kMaxGroups];     // hom_sum operands (tiled arrays)
   int32_t ngroups;
   int32_t w;                           // window width for hom_scal
+};
+
+// Encrypted matrix-vector product of Eq. (itq2):
+// out_i = alpha_i * prod_j s_j^{b_ij} mod n^2, rows grouped by edge node.
+template <int L2>
+struct MatvecParams {
+  ModConst<L2> m;
+  int32_t c;       // bucket window (bits); 2^c buckets per row
+  int32_t nwin;    // windows covering the widest b_ij
+  int32_t ntiles;  // row tiles (a tile = one CTA's rows, all of one node)
+  int32_t pad_;
 };
 
 }  // namespace pc2

@@ -278,3 +278,127 @@ def hom_scal(ctx: Context, key: Key, ct, k, count: int, out=None, stream=None):
     out = empty_tiled(count, 2 * key.limbs, ct.device) if out is None else out
     _check(_hom_scal(ctx.h, key.h, _ptr(ct), _ptr(k), count, _ptr(out), _stream(stream)), "pc2_hom_scal")
     return out
+
+
+# ------------------------------------------------------------------ quantizer and ADMM
+_quantize = _sig("pc2_quantize", [_vp, _vp, _sz, ctypes.c_double, ctypes.c_double, _i, _i, _i, _vp, _vp])
+
+
+class _AdmmParams(ctypes.Structure):
+    _fields_ = [("nodes", _i), ("node_sizes", ctypes.POINTER(_i)), ("lambda_", ctypes.c_double),
+                ("rho", ctypes.c_double), ("zmin", ctypes.c_double), ("zmax", ctypes.c_double),
+                ("log2_scale", _i), ("seed", _u64), ("per_node", _i)]
+
+
+_admm_create = _sig("pc2_admm_create", [_vp, _vp, ctypes.POINTER(_AdmmParams), _vp, _vp, ctypes.POINTER(_vp), _vp])
+_admm_destroy = _sig("pc2_admm_destroy", [_vp], None)
+_admm_reset = _sig("pc2_admm_reset", [_vp, _vp])
+_admm_round = _sig("pc2_admm_round", [_vp, _i, _vp])
+_admm_round_plain = _sig("pc2_admm_round_plain", [_vp, _i, _vp])
+_admm_get = _sig("pc2_admm_get", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32), _vp])
+_admm_set = _sig("pc2_admm_set", [_vp, _vp, _vp, _vp, _u32, _vp])
+_admm_buffers = _sig("pc2_admm_buffers", [_vp] + [ctypes.POINTER(_vp)] * 5 + [ctypes.POINTER(_i)])
+_admm_info = _sig("pc2_admm_info", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)])
+
+
+def quantize(ctx: Context, u, zmin: float, zmax: float, log2_scale: int, gamma: int = 2, negate: bool = False,
+             out=None, stream=None):
+    """Eq. (et21) on a float64 tensor; returns an int64 tensor of uint64 codes."""
+    import torch
+
+    out = torch.empty(u.numel(), dtype=torch.int64, device=u.device) if out is None else out
+    _check(_quantize(ctx.h, _ptr(u), u.numel(), zmin, zmax, log2_scale, gamma, int(negate), _ptr(out),
+                     _stream(stream)), "pc2_quantize")
+    return out
+
+
+class Admm:
+    """Algorithm 1 of the paper on one GPU (see include/pc2.h)."""
+
+    def __init__(self, ctx: Context, key: Key, node_sizes, alpha, Bbar, lam: float, rho: float, zmin: float,
+                 zmax: float, log2_scale: int, seed: int, per_node: bool = False, stream=None):
+        sizes = (_i * len(node_sizes))(*[int(s) for s in node_sizes])
+        self._sizes = sizes
+        p = _AdmmParams(len(node_sizes), sizes, lam, rho, zmin, zmax, log2_scale, seed, int(per_node))
+        h = _vp()
+        _check(_admm_create(ctx.h, key.h, ctypes.byref(p), _ptr(alpha), _ptr(Bbar), ctypes.byref(h), _stream(stream)),
+               "pc2_admm_create")
+        self.h = h
+        self.N = int(sum(node_sizes))
+        self.ctx, self.key = ctx, key
+
+    def close(self):
+        if self.h:
+            _admm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        _check(_admm_reset(self.h, _stream(stream)), "pc2_admm_reset")
+
+    def round(self, rounds: int = 1, stream=None):
+        _check(_admm_round(self.h, rounds, _stream(stream)), "pc2_admm_round")
+
+    def round_plain(self, rounds: int = 1, stream=None):
+        _check(_admm_round_plain(self.h, rounds, _stream(stream)), "pc2_admm_round_plain")
+
+    def get(self, stream=None):
+        import torch
+
+        x, z, v = (torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(3))
+        r = _u32()
+        _check(_admm_get(self.h, _ptr(x), _ptr(z), _ptr(v), ctypes.byref(r), _stream(stream)), "pc2_admm_get")
+        return x, z, v, r.value
+
+    def set(self, x, z, v, round_: int, stream=None):
+        _check(_admm_set(self.h, _ptr(x), _ptr(z), _ptr(v), round_, _stream(stream)), "pc2_admm_set")
+
+    def buffers(self) -> dict:
+        ps = [_vp() for _ in range(5)]
+        n = _i()
+        _check(_admm_buffers(self.h, *[ctypes.byref(p) for p in ps], ctypes.byref(n)), "pc2_admm_buffers")
+        return dict(zip(["zhat", "vhat", "xhat", "alpha_hat", "D"], [p.value for p in ps]), N=n.value)
+
+    def info(self) -> dict:
+        c, nw, nt = _i(), _i(), _i()
+        _check(_admm_info(self.h, ctypes.byref(c), ctypes.byref(nw), ctypes.byref(nt)), "pc2_admm_info")
+        return {"c": c.value, "nwin": nw.value, "ntiles": nt.value}
+
+
+def device_words(ptr: int, nwords: int, device="cuda"):
+    """A torch view-copy of `nwords` 32-bit words at a library-owned device pointer (for tests)."""
+    import torch
+
+    out = torch.empty(nwords, dtype=torch.int32, device=device)
+    torch.cuda.synchronize()
+    _lib_copy(out.data_ptr(), ptr, nwords * 4)
+    return out
+
+
+def _lib_copy(dst: int, src: int, nbytes: int):
+    import torch
+
+    # torch has no raw-pointer view; use cudaMemcpy through the CUDA runtime torch links against
+    rt = ctypes.CDLL(_cudart_path())
+    rt.cudaMemcpy.argtypes = [_vp, _vp, _sz, _i]
+    rt.cudaMemcpy.restype = _i
+    if rt.cudaMemcpy(dst, src, nbytes, 3) != 0:  # cudaMemcpyDeviceToDevice
+        raise RuntimeError("cudaMemcpy failed")
+    torch.cuda.synchronize()
+
+
+def _cudart_path() -> str:
+    import glob as _g
+
+    import torch
+
+    cands = _g.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libcudart*.so*"))
+    cands += _g.glob("/usr/local/cuda/lib64/libcudart.so*")
+    if not cands:
+        raise RuntimeError("libcudart not found")
+    return cands[0]

@@ -1,0 +1,143 @@
+"""GPU parity of the private ADMM round (Algorithm 1) against the oracle.
+
+Setup integers come from the same FP64 set-up (oracle.admm.dis_setup) on both
+sides, so the decrypted integers, the exact decode and therefore every
+iterate are bit-identical; ciphertexts are bit-identical given the same
+Philox draws.  The plaintext Dis-ADMM path differs only in summation order
+(relative 1e-9)."""
+import numpy as np
+import pytest
+
+from oracle import admm as O
+from oracle import paillier as P
+from paper_2601_14980_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+QP = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    return torch, pc2, pc2.Context(0)
+
+
+def _make(env, L, nbits, seed=1, per_node=False, key_seed=1):
+    torch, pc2, ctx = env
+    st = O.dis_setup(L.A, L.y, W.node_sizes(L.A.shape[1], L.K), L.rho)
+    p, q = W.primes(nbits, key_seed)
+    kg, ko = pc2.Key.from_primes(p, q), P.derive_key(p, q)
+    alpha = torch.from_numpy(np.concatenate(st.alpha)).cuda()
+    Bbar = torch.from_numpy(np.concatenate([b.ravel() for b in st.Bbar])).cuda()
+    adm = pc2.Admm(ctx, kg, st.sizes, alpha, Bbar, L.lam, L.rho, QP.zmin, QP.zmax, QP.log2_scale, seed,
+                   per_node=per_node)
+    return st, kg, ko, adm
+
+
+def _ints(pc2, ptr, count, limbs):
+    w = pc2.device_words(ptr, pc2.tiled_words(count, limbs))
+    return w
+
+
+def test_private_rounds_match_oracle_bit_exact(env):
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=1)                  # 128 x 256, 4 nodes, lambda 0.01, rho 1, 5 rounds
+    st, kg, ko, adm = _make(env, L, 1024)
+    ref = O.quantized_admm(st, L.lam, L.rho, L.iters, QP)
+    for t in range(L.iters):
+        adm.round(1)                           # round 1 eager, later rounds replay the CUDA graph
+        x, z, v, nxt = adm.get()
+        assert nxt == t + 2
+        assert np.array_equal(x.cpu().numpy(), ref.x[t]), t
+        assert np.array_equal(z.cpu().numpy(), ref.z[t]), t
+        assert np.array_equal(v.cpu().numpy(), ref.v[t]), t
+        b = adm.buffers()
+        D = pc2.tiled_to_ints(ctx, _ints(pc2, b["D"], 256, kg.limbs), 256, kg.limbs)
+        assert D == ref.D[t], t
+    assert ctx.status() == 0
+    # ciphertexts of the last round, sampled: z-hat, (-v)-hat and x-hat rows
+    T = L.iters
+    zprev = ref.z[T - 2] if T > 1 else np.zeros(256)
+    vprev = ref.v[T - 2] if T > 1 else np.zeros(256)
+    zq, vq = O.gamma2(zprev, QP), O.gamma2(-vprev, QP)
+    b = adm.buffers()
+    zh = pc2.tiled_to_ints(ctx, _ints(pc2, b["zhat"], 256, 2 * kg.limbs), 256, 2 * kg.limbs)
+    vh = pc2.tiled_to_ints(ctx, _ints(pc2, b["vhat"], 256, 2 * kg.limbs), 256, 2 * kg.limbs)
+    xh = pc2.tiled_to_ints(ctx, _ints(pc2, b["xhat"], 256, 2 * kg.limbs), 256, 2 * kg.limbs)
+    ah = pc2.tiled_to_ints(ctx, _ints(pc2, b["alpha_hat"], 256, 2 * kg.limbs), 256, 2 * kg.limbs)
+    for e in (0, 63, 64, 200, 255):
+        assert zh[e] == P.encrypt(ko, [int(zq[e])], [P.r_of(ko, 1, O.stream_id(T, O.KIND_Z), e)])[0]
+        assert vh[e] == P.encrypt(ko, [int(vq[e])], [P.r_of(ko, 1, O.stream_id(T, O.KIND_V), e)])[0]
+    # x-hat rows 0 and 130 recomputed by the oracle's Eq. (itq2) from the GPU's own alpha-hat, s-hat
+    bq = [O.gamma2(B, QP) for B in st.Bbar]
+    s = P.hom_add(ko, zh, vh)
+    for i in (0, 130):
+        k, o = i // 64, (i // 64) * 64
+        row = bq[k][i - o:i - o + 1].astype(np.uint64)
+        assert xh[i] == P.hom_matvec(ko, [ah[i]], s[o:o + 64], row)[0]
+
+
+def test_tiny_problem_against_real_encryption_oracle(env):
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=11, M=10, N=12, nnz=3, K=2)
+    st, kg, ko, adm = _make(env, L, 256, seed=1234, key_seed=9)
+    pr = O.private_admm(st, 0.01, 1.0, 3, QP, ko, seed=1234)
+    for t in range(3):
+        adm.round(1)
+        x, z, v, _ = adm.get()
+        assert np.array_equal(x.cpu().numpy(), pr.x[t]) and np.array_equal(z.cpu().numpy(), pr.z[t])
+        b = adm.buffers()
+        for name, ref in (("zhat", pr.zhat[t]), ("vhat", pr.vhat[t]), ("xhat", pr.xhat[t])):
+            got = pc2.tiled_to_ints(ctx, _ints(pc2, b[name], 12, 2 * kg.limbs), 12, 2 * kg.limbs)
+            assert got == ref, (name, t)
+
+
+def test_per_node_path_equals_batched(env):
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=2, M=64, N=200, nnz=10, K=3)   # uneven nodes 67/67/66, not tile aligned
+    _, _, _, a1 = _make(env, L, 512, seed=5)
+    _, _, _, a2 = _make(env, L, 512, seed=5, per_node=True)
+    a1.round(3)
+    a2.round(3)
+    for u, w in zip(a1.get()[:3], a2.get()[:3]):
+        assert torch.equal(u, w)
+
+
+def test_plain_dis_admm_and_checkpoint(env):
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=3)
+    st, kg, ko, adm = _make(env, L, 1024)
+    adm.round_plain(7)
+    x, z, v, _ = adm.get()
+    xr, zr, vr = O.dis_admm(st, L.lam, L.rho, 7)
+    np.testing.assert_allclose(x.cpu().numpy(), xr, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(z.cpu().numpy(), zr, rtol=1e-9, atol=1e-12)
+    # checkpoint / resume: 2 rounds, save, 3 more on a fresh object == 5 rounds
+    adm.reset()
+    adm.round(2)
+    x2, z2, v2, r2 = adm.get()
+    _, _, _, adm_b = _make(env, L, 1024)
+    adm_b.set(x2, z2, v2, r2)
+    adm_b.round(3)
+    adm.round(3)
+    for u, w in zip(adm.get()[:3], adm_b.get()[:3]):
+        assert torch.equal(u, w)
+
+
+def test_quantize_entry_point(env):
+    torch, pc2, ctx = env
+    u = np.array([-8.0, 8.0, 0.0, -7.999999, 1.5, 0.1, -8.0 + 5.5 / 2**24, 3.25])
+    du = torch.from_numpy(u).cuda()
+    q2 = pc2.quantize(ctx, du, -8.0, 8.0, 24, gamma=2).cpu().numpy()
+    assert np.array_equal(q2, O.gamma2(u, QP))
+    q1 = pc2.quantize(ctx, du, -8.0, 8.0, 24, gamma=1).cpu().numpy()
+    assert np.array_equal(q1, O.gamma1(u, QP))
+    qn = pc2.quantize(ctx, du, -8.0, 8.0, 24, gamma=2, negate=True).cpu().numpy()
+    assert np.array_equal(qn, O.gamma2(-u, QP))
+    assert ctx.status() == 0
+    pc2.quantize(ctx, torch.tensor([9.0], dtype=torch.float64, device="cuda"), -8.0, 8.0, 24)
+    assert ctx.status() & pc2.ST_QUANT
