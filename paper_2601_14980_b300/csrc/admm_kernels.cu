@@ -406,7 +406,7 @@ int matvec_grid(int ntiles, int sms) {
 PC2_ADMM_INST(16, 1)
 PC2_ADMM_INST(32, 1)
 PC2_ADMM_INST(64, 1)
-PC2_ADMM_INST(128, 2)
+PC2_ADMM_INST(128, 4)
 PC2_ADMM_INST(192, 4)
 
 }  // namespace pc2

@@ -117,30 +117,11 @@ __device__ __forceinline__ void row_mac(uint32_t (&t)[S], uint32_t& c0, uint32_t
   addc_z(c1);
 }
 
-// a <- a * b / R mod N.  a: this lane's segment (registers, a < R);
-// b: the group's operand in shared memory, word i at bcol[i * bstride] (b < N).
+// Final step of mont_mul: t (this lane's words) plus the carry
+// word (c0, c1) above the segment is < 2N; write t - N or t into a.
 template <int S, int T, class NS>
-__device__ __forceinline__ void mont_mul(uint32_t (&a)[S], const uint32_t* __restrict__ bcol, int bstride, const NS& n,
-                                         uint32_t np, const Grp<T>& g) {
-  constexpr int L = S * T;
-  uint32_t t[S];
-#pragma unroll
-  for (int j = 0; j < S; ++j) t[j] = 0u;
-  uint32_t c0 = 0u, c1 = 0u;
-  const RegA<S> av{a};
-#pragma unroll 1
-  for (int i = 0; i < L; ++i) {
-    const uint32_t b = bcol[i * bstride];
-    row_mac<S>(t, c0, c1, av, b);
-    const uint32_t m = g.bcast(t[0] * np, 0);
-    row_mac<S>(t, c0, c1, n, m);
-    const uint32_t up = g.from_next(t[0]);
-#pragma unroll
-    for (int j = 0; j < S - 1; ++j) t[j] = t[j + 1];
-    asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(t[S - 1]) : "r"(up), "r"(c0));
-    asm volatile("addc.u32 %0, %1, 0;" : "=r"(c0) : "r"(c1));
-    c1 = 0u;
-  }
+__device__ __forceinline__ void mont_finish(uint32_t (&a)[S], uint32_t (&t)[S], uint32_t c0, uint32_t c1, const NS& n,
+                                            const Grp<T>& g) {
   if constexpr (T == 1) {
     // t + c0 R < 2N: subtract N when c0 != 0 or t >= N.
     uint32_t br;
@@ -192,6 +173,33 @@ __device__ __forceinline__ void mont_mul(uint32_t (&a)[S], const uint32_t* __res
 #pragma unroll
     for (int j = 0; j < S; ++j) a[j] = sub ? a[j] : t[j];
   }
+}
+
+// a <- a * b / R mod N.  a: this lane's segment (registers, a < R);
+// b: the group's operand in shared memory, word i at bcol[i * bstride] (b < N).
+template <int S, int T, class NS>
+__device__ __forceinline__ void mont_mul(uint32_t (&a)[S], const uint32_t* __restrict__ bcol, int bstride, const NS& n,
+                                         uint32_t np, const Grp<T>& g) {
+  constexpr int L = S * T;
+  uint32_t t[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) t[j] = 0u;
+  uint32_t c0 = 0u, c1 = 0u;
+  const RegA<S> av{a};
+#pragma unroll 1
+  for (int i = 0; i < L; ++i) {
+    const uint32_t b = bcol[i * bstride];
+    row_mac<S>(t, c0, c1, av, b);
+    const uint32_t m = g.bcast(t[0] * np, 0);
+    row_mac<S>(t, c0, c1, n, m);
+    const uint32_t up = g.from_next(t[0]);
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) t[j] = t[j + 1];
+    asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(t[S - 1]) : "r"(up), "r"(c0));
+    asm volatile("addc.u32 %0, %1, 0;" : "=r"(c0) : "r"(c1));
+    c1 = 0u;
+  }
+  mont_finish<S, T>(a, t, c0, c1, n, g);
 }
 
 // ---------------------------------------------------------------- columns

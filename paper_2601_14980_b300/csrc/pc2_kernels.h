@@ -35,7 +35,9 @@ int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* 
 int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st);
 int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st);
 
-// Lanes per element for each modulus width (registers: 2 segments + modulus).
-constexpr int lanes_for(int L) { return L <= 96 ? 1 : (L <= 128 ? 2 : 4); }
+// Lanes per element for each modulus width: the row core keeps a segment of
+// the multiplicand and of the accumulator in registers (plus the modulus
+// segment when T > 1); wider operands are split across lanes.
+constexpr int lanes_for(int L) { return L <= 64 ? 1 : (L <= 96 ? 2 : 4); }
 
 }  // namespace pc2
