@@ -72,6 +72,19 @@ size_t pc2_ctx_scratch_bytes(const pc2_ctx* ctx);
 int pc2_ctx_status(pc2_ctx* ctx, pc2_stream_t stream, int* bits);
 /* Forces the sliding-window width (3..6) of subsequent exponentiations; 0 = automatic. */
 int pc2_ctx_set_window(pc2_ctx* ctx, int w);
+/* Forces the lanes per element (1, 2, 4, 8) of the exponentiation kernels where
+ * that count is built for the operand size; 0 = automatic (autotuned entry for
+ * the call's size class if any, else the largest lane count whose element
+ * groups still fit in one resident wave: small batches get more lanes per
+ * element and finish sooner). */
+int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes);
+/* Autotuner: times every built lane count x window width (4..6) of key-owner
+ * encryption (ops bit 0) and/or decryption (bit 1) on `count` elements (at
+ * most two resident waves of them) and records the fastest for calls of the
+ * same size class (ceil(log2 count)) on this key size in this context.
+ * h_result (optional) receives (lanes, window) per tuned op, in that order.
+ * Allocates and frees temporary device buffers; synchronises `stream`. */
+int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_stream_t stream, int* h_result);
 
 /* ---- keys (host) ------------------------------------------------------ *
  * Sec. III-B: n = pq, lambda = lcm(p-1, q-1), g = n + 1 (so g^m = 1 + mn and

@@ -9,6 +9,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <utility>
 
 #include "../../include/pc2.h"
@@ -67,12 +68,69 @@ static uint32_t* ctx_scratch(void* c, size_t bytes) {
 
 uint32_t* ctx_scratch_get(pc2_ctx* ctx, size_t bytes) { return ctx_scratch(ctx, bytes); }
 
+// Lane counts built per operation and limb count (inst_crt_*.cu).
+const int* lane_set(int op, int limbs, int* n) {
+  static const int s1[] = {1}, s124[] = {1, 2, 4}, s1248[] = {1, 2, 4, 8}, s248[] = {2, 4, 8};
+  (void)op;
+  switch (limbs) {
+    case 8: *n = 3; return s124;
+    case 16: case 32: case 64: *n = 4; return s1248;
+    case 96: *n = 3; return s248;
+  }
+  *n = 1;
+  return s1;
+}
+
+static int log2_bucket(size_t count) {
+  int b = 0;
+  while (((size_t)1 << b) < count && b < 62) ++b;
+  return b;
+}
+
+std::pair<int, int> pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
+  int n = 0;
+  const int* set = lane_set(op, limbs, &n);
+  if (ctx->lanes)
+    for (int i = 0; i < n; ++i)
+      if (set[i] == ctx->lanes) return {ctx->lanes, 0};
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tuned.find(std::make_tuple(op, limbs, log2_bucket(count)));
+    if (it != ctx->tuned.end()) return it->second;
+  }
+  // the largest lane count whose groups still fit in one resident wave
+  // (about 384 threads per SM for these kernels)
+  const double cap = (double)ctx->sms * 384.0;
+  int T = set[0];
+  for (int i = 0; i < n; ++i)
+    if ((double)count * set[i] <= cap) T = set[i];
+  return {T, 0};
+}
+
+template <int Lh, int T>
+constexpr bool crt_has() {
+  return (Lh == 8 && T <= 4) || ((Lh == 16 || Lh == 32 || Lh == 64) && T <= 8) || (Lh == 96 && T >= 2 && T <= 8);
+}
+// Calls fn(std::integral_constant<int, T>) for a built lane count T.
+template <int Lh, class Fn>
+static int with_crt_lanes(int T, Fn fn) {
+  switch (T) {
+    case 1: if constexpr (crt_has<Lh, 1>()) return fn(std::integral_constant<int, 1>()); break;
+    case 2: if constexpr (crt_has<Lh, 2>()) return fn(std::integral_constant<int, 2>()); break;
+    case 4: if constexpr (crt_has<Lh, 4>()) return fn(std::integral_constant<int, 4>()); break;
+    case 8: if constexpr (crt_has<Lh, 8>()) return fn(std::integral_constant<int, 8>()); break;
+  }
+  return PC2_EUNSUPPORTED;
+}
+
 template <int Lh>
 static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
                    uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
+  const auto cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
+  const int w = cfg.second ? cfg.second : ctx->window;
   int rc;
-  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, ctx->window,
-                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, ctx->window, P); }, &rc);
+  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w,
+                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, w, P); }, &rc);
   if (!P0) return rc;
   std::unique_ptr<EncCrtParams<Lh>> P(new (std::nothrow) EncCrtParams<Lh>(*P0));
   if (!P) return PC2_ENOMEM;
@@ -80,16 +138,21 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->stream = stream;
   P->e0 = e0;
   P->mwords = mw ? Lh : 2;
-  return launch_enc_crt<Lh, lanes_for(Lh)>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
+    return launch_enc_crt<Lh, decltype(tt)::value>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms,
+                                                   st, 0);
+  });
 }
 
 template <int Lh>
 static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, size_t count, uint64_t seed,
                          const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* out, cudaStream_t st,
                          size_t base) {
+  const auto cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
+  const int w = cfg.second ? cfg.second : ctx->window;
   int rc;
-  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, ctx->window,
-                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, ctx->window, P); }, &rc);
+  auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w,
+                                     [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, w, P); }, &rc);
   if (!P0) return rc;
   std::unique_ptr<EncCrtParams<Lh>> P(new (std::nothrow) EncCrtParams<Lh>(*P0));
   if (!P) return PC2_ENOMEM;
@@ -98,8 +161,10 @@ static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, 
   P->mwords = 2;
   P->round_ptr = round_ptr;
   P->kind = kind;
-  return launch_enc_crt<Lh, lanes_for(Lh)>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st,
-                                           base);
+  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
+    return launch_enc_crt<Lh, decltype(tt)::value>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status,
+                                                   ctx->sms, st, base);
+  });
 }
 
 int encrypt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
@@ -136,11 +201,14 @@ static int enc_pub(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
 template <int Lh>
 static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
                size_t base = 0) {
+  const auto cfg = pick_config(ctx, OP_DEC, Lh, count);
+  const int w = cfg.second ? cfg.second : ctx->window;
   int rc;
-  auto P = cached<DecParams<Lh>>(key, KIND_DEC, ctx->window,
-                                 [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, ctx->window, p); }, &rc);
+  auto P = cached<DecParams<Lh>>(key, KIND_DEC, w, [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, w, p); }, &rc);
   if (!P) return rc;
-  return launch_dec_crt<Lh, lanes_for(Lh)>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
+  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
+    return launch_dec_crt<Lh, decltype(tt)::value>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
+  });
 }
 
 template <int Lh>
@@ -302,6 +370,83 @@ int pc2_ctx_set_window(pc2_ctx* ctx, int w) {
   if (!ctx || (w != 0 && (w < 3 || w > kMaxWin))) return PC2_EINVAL;
   ctx->window = w;
   return PC2_OK;
+}
+
+int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes) {
+  if (!ctx || (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)) return PC2_EINVAL;
+  ctx->lanes = lanes;
+  return PC2_OK;
+}
+
+int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_stream_t stream, int* h_result) {
+  if (!ctx || !key || !count || (ops & ~3) || !ops) return PC2_EINVAL;
+  if (!key->priv) return PC2_EKEY;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int Lh = key->Lh;
+  // time at most two resident waves; larger counts of the same size class
+  // behave the same per wave
+  const size_t cap = (size_t)ctx->sms * 384 * 2;
+  const size_t n = count < cap ? count : cap;
+  uint64_t* dm = nullptr;
+  uint32_t *dct = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dm, n * 8) != cudaSuccess) return PC2_ENOMEM;
+  if (cudaMalloc(&dct, pc2_tiled_words(n, 2 * Lh) * 4) != cudaSuccess ||
+      cudaMalloc(&dout, pc2_tiled_words(n, Lh) * 4) != cudaSuccess) {
+    cudaFree(dm);
+    cudaFree(dct);
+    return PC2_ENOMEM;
+  }
+  cudaMemsetAsync(dm, 0x5a, n * 8, st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved_lanes = ctx->lanes, saved_window = ctx->window;
+  int rc = PC2_OK, res_i = 0;
+  for (int op : {OP_ENC_CRT, OP_DEC}) {
+    if (!((op == OP_ENC_CRT && (ops & 1)) || (op == OP_DEC && (ops & 2)))) continue;
+    int nl = 0;
+    const int* set = lane_set(op, Lh, &nl);
+    float best = 1e30f;
+    std::pair<int, int> pick{set[0], 0};
+    for (int i = 0; i < nl && rc == PC2_OK; ++i) {
+      for (int w = 4; w <= kMaxWin && rc == PC2_OK; ++w) {
+        ctx->lanes = set[i];
+        ctx->window = w;
+        // decryption times the ciphertexts of the encryption pass (made once below when only ops == 2)
+        if (op == OP_DEC && !(ops & 1) && i == 0 && w == 4) rc = pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream);
+        if (rc != PC2_OK) break;
+        cudaEventRecord(e0, st);
+        rc = op == OP_ENC_CRT ? pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream)
+                              : pc2_decrypt(ctx, key, dct, n, dout, stream);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = PC2_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == PC2_OK && ms < best) {
+          best = ms;
+          pick = {set[i], w};
+        }
+      }
+    }
+    if (rc != PC2_OK) break;
+    {
+      std::lock_guard<std::mutex> g(ctx->tune_mu);
+      ctx->tuned[std::make_tuple(op, Lh, log2_bucket(count))] = pick;
+    }
+    if (h_result) {
+      h_result[res_i++] = pick.first;
+      h_result[res_i++] = pick.second;
+    }
+  }
+  ctx->lanes = saved_lanes;
+  ctx->window = saved_window;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(dm);
+  cudaFree(dct);
+  cudaFree(dout);
+  return rc;
 }
 
 int pc2_keygen(int nbits, uint64_t seed, pc2_key** out) {

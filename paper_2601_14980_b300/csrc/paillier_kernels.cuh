@@ -16,6 +16,7 @@
 // elements; each element is owned by a group of T lanes (mont.cuh).  Scratch
 // (global memory, from the context) holds each group's window table and glue
 // columns, interleaved by group so that a warp's accesses coalesce.
+#pragma once
 #include <cuda_runtime.h>
 
 #include "mont.cuh"
@@ -372,159 +373,5 @@ __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_scal(const 
     }
   }
 }
-
-// ------------------------------------------------------------------ layout conversion
-__global__ void k_pack(const uint32_t* __restrict__ canon, size_t count, int Lc, uint32_t* __restrict__ tiled) {
-  const size_t total = count * (size_t)Lc;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t e = i / (size_t)Lc;
-    const int j = (int)(i % (size_t)Lc);
-    tiled[tiled_index(e, j, Lc)] = canon[i];
-  }
-}
-__global__ void k_unpack(const uint32_t* __restrict__ tiled, size_t count, int Lc, uint32_t* __restrict__ canon) {
-  const size_t total = count * (size_t)Lc;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t e = i / (size_t)Lc;
-    const int j = (int)(i % (size_t)Lc);
-    canon[i] = tiled[tiled_index(e, j, Lc)];
-  }
-}
-
-// ------------------------------------------------------------------ launchers
-template <class K>
-static int occupancy_grid(K kern, size_t smem, int sms) {
-  int per = 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem) != cudaSuccess) return -1;
-  if (per < 1) return -1;
-  return per * sms;
-}
-
-template <int Lh, int T>
-int launch_enc_crt(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
-                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base) {
-  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
-  auto kern = k_enc_crt<Lh, T>;
-  const int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
-  const int tabw = (1 << (w - 1)) * Lh;
-  const size_t per_group = (size_t)tabw + 8 * (size_t)(2 * Lh + 4);
-  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
-  if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status, base);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-template <int L2, int T>
-int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
-                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st) {
-  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
-  auto kern = k_enc_pub<L2, T>;
-  const int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const int tabw = (1 << (P.e.w - 1)) * L2;
-  const size_t per_group = (size_t)tabw + 4 * (size_t)(L2 + 4);
-  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
-  if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-template <int Lh, int T>
-int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
-                   void* sctx, int sms, cudaStream_t st, size_t base) {
-  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
-  auto kern = k_dec_crt<Lh, T>;
-  const int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
-  const int tabw = (1 << (w - 1)) * Lh;
-  const size_t per_group = (size_t)tabw + 7 * (size_t)(2 * Lh + 4);
-  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
-  if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw, base);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-// Decryption into a fixed scratch region of `scratch_words` words: the
-// persistent grid is cut down to the CTAs whose scratch fits.
-template <int Lh, int T>
-int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, uint32_t* scratch,
-                         size_t scratch_words, int sms, cudaStream_t st) {
-  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
-  auto kern = k_dec_crt<Lh, T>;
-  int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
-  const int tabw = (1 << (w - 1)) * Lh;
-  const size_t per_cta = ((size_t)tabw + 7 * (size_t)(2 * Lh + 4)) * (kThreads / T);
-  if (per_cta > scratch_words) return PC2_ERANGE;
-  const size_t fit = scratch_words / per_cta;
-  if ((size_t)grid > fit) grid = (int)fit;
-  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw, (size_t)0);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-template <int L2, int T>
-int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms, cudaStream_t st, size_t base) {
-  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
-  auto kern = k_hom_sum<L2, T>;
-  int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const size_t groups_needed = (count + (kThreads / T) - 1) / (kThreads / T);
-  if ((size_t)grid > groups_needed) grid = (int)groups_needed;
-  kern<<<grid, kThreads, smem, st>>>(P, count, out, base);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-template <int L2, int T>
-int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* k, size_t count, uint32_t* out,
-                    ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st) {
-  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
-  auto kern = k_hom_scal<L2, T>;
-  const int grid = occupancy_grid(kern, smem, sms);
-  if (grid < 0) return PC2_ECUDA;
-  const size_t per_group = (size_t)(1 << P.w) * L2;
-  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
-  if (!scratch) return PC2_ENOMEM;
-  kern<<<grid, kThreads, smem, st>>>(P, ct, k, count, out, scratch);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st) {
-  k_pack<<<sms * 8, 256, 0, st>>>(canon, count, Lc, tiled);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st) {
-  k_unpack<<<sms * 8, 256, 0, st>>>(tiled, count, Lc, canon);
-  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
-}
-
-// Supported sizes: n of 256, 512, 1024, 2048 or 3072 bits.
-#define PC2_INST_H(Lh, T)                                                                                         \
-  template int launch_enc_crt<Lh, T>(const EncCrtParams<Lh>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
-                                     ScratchFn, void*, int*, int, cudaStream_t, size_t);                           \
-  template int launch_dec_crt<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*,   \
-                                     int, cudaStream_t, size_t);                                                   \
-  template int launch_dec_crt_fixed<Lh, T>(const DecParams<Lh>&, const uint32_t*, size_t, uint32_t*, uint32_t*,     \
-                                           size_t, int, cudaStream_t);
-#define PC2_INST_2(L2, T)                                                                                         \
-  template int launch_enc_pub<L2, T>(const EncPubParams<L2>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, \
-                                     ScratchFn, void*, int*, int, cudaStream_t);                                   \
-  template int launch_hom_sum<L2, T>(const HomParams<L2>&, size_t, uint32_t*, int, cudaStream_t, size_t);          \
-  template int launch_hom_scal<L2, T>(const HomParams<L2>&, const uint32_t*, const uint64_t*, size_t, uint32_t*,   \
-                                      ScratchFn, void*, int, cudaStream_t);
-PC2_INST_H(8, 1)
-PC2_INST_H(16, 1)
-PC2_INST_H(32, 1)
-PC2_INST_H(64, 1)
-PC2_INST_H(96, 2)
-PC2_INST_2(16, 1)
-PC2_INST_2(32, 1)
-PC2_INST_2(64, 1)
-PC2_INST_2(128, 4)
-PC2_INST_2(192, 4)
 
 }  // namespace pc2

@@ -402,3 +402,26 @@ def _cudart_path() -> str:
     if not cands:
         raise RuntimeError("libcudart not found")
     return cands[0]
+
+
+_ctx_set_lanes = _sig("pc2_ctx_set_lanes", [_vp, _i])
+_autotune = _sig("pc2_autotune", [_vp, _vp, _sz, _i, _vp, ctypes.POINTER(_i)])
+
+
+def set_lanes(ctx: Context, lanes: int):
+    """Force lanes per element (1, 2, 4, 8) where built; 0 = automatic."""
+    _check(_ctx_set_lanes(ctx.h, lanes), "pc2_ctx_set_lanes")
+
+
+def autotune(ctx: Context, key: Key, count: int, encrypt: bool = True, decrypt: bool = True, stream=None) -> dict:
+    """Run the library's autotuner for `count`-element calls; returns the chosen (lanes, window) per op."""
+    ops = (1 if encrypt else 0) | (2 if decrypt else 0)
+    res = (_i * 4)()
+    _check(_autotune(ctx.h, key.h, count, ops, _stream(stream), res), "pc2_autotune")
+    out, i = {}, 0
+    if encrypt:
+        out["encrypt"] = (res[0], res[1])
+        i = 2
+    if decrypt:
+        out["decrypt"] = (res[i], res[i + 1])
+    return out
