@@ -397,7 +397,7 @@ __device__ __forceinline__ void g_addmod(const Col& d, const Col& a, const Col& 
 }
 // Word-serial CIOS: d = a * b / R mod N, R = 2^(32 len); a < R, b < N.
 // t: temporary column of len + 2 words.  d may alias a or b.
-static __device__ __noinline__ void g_mont(const Col d, const Col a, const Col b, const uint32_t* N, uint32_t np, int len,
+__device__ __forceinline__ void g_mont(const Col d, const Col a, const Col b, const uint32_t* N, uint32_t np, int len,
                                     const Col t) {
   for (int j = 0; j < len + 2; ++j) t[j] = 0u;
   for (int i = 0; i < len; ++i) {

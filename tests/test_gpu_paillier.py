@@ -141,7 +141,7 @@ def test_full_size_2048_sampled(env):
         assert int.from_bytes(decw[i * kg.limbs:(i + 1) * kg.limbs].tobytes(), "little") == expect
 
 
-@pytest.mark.parametrize("nbits", [256, 1024, 2048])
+@pytest.mark.parametrize("nbits", [256, 512, 1024, 2048])
 def test_lanes_and_windows_bit_identical(env, nbits):
     """Every built lanes-per-element count and window width computes the same ciphertexts and plaintexts."""
     torch, pc2, ctx = env
