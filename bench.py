@@ -131,6 +131,67 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _admm_setup(L, sizes):
+    """Edge-node initialisation of Sec. II (input preparation, not timed):
+    B_k = (A_k^T A_k + rho I)^-1, alpha_k = B_k A_k^T y, Bbar_k = rho B_k."""
+    import numpy as np
+
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    alpha, Bbar = [], []
+    for k in range(len(sizes)):
+        Ak = L.A[:, off[k]:off[k + 1]]
+        Bk = np.linalg.inv(Ak.T @ Ak + L.rho * np.eye(sizes[k]))
+        alpha.append(Bk @ (Ak.T @ L.y))
+        Bbar.append((L.rho * Bk).ravel())
+    return np.concatenate(alpha), np.concatenate(Bbar)
+
+
+def run_admm(dev, rounds: int = 5):
+    """Seconds per ADMM iteration on the small LASSO workload (1024-bit n,
+    4 nodes): batched rounds (one graph per round) vs the per-node path."""
+    import numpy as np
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+    from paper_2601_14980_b300 import workloads as W
+
+    L = W.lasso_small(seed=1)
+    sizes = W.node_sizes(L.A.shape[1], L.K)
+    alpha, Bbar = _admm_setup(L, sizes)
+    da, dB = torch.from_numpy(alpha).to(dev), torch.from_numpy(Bbar).to(dev)
+    ctx = pc2.Context(dev)
+    key = pc2.Key.generate(1024, 2026)
+    out = {}
+    st = torch.cuda.current_stream()
+    for name, per_node in (("batched", False), ("per_node", True)):
+        adm = pc2.Admm(ctx, key, sizes, da, dB, L.lam, L.rho, -8.0, 8.0, 24, 77, per_node=per_node)
+        adm.round(2)                      # warm-up (first round eager, graph captured)
+        adm.reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        adm.round(rounds)
+        b.record(st)
+        b.synchronize()
+        out[name] = a.elapsed_time(b) / 1e3 / rounds
+        if name == "batched":
+            x = adm.get()[0].cpu().numpy()
+            out["mse"] = float(np.mean((x - L.x0) ** 2))
+            adm.reset()
+            torch.cuda.synchronize()
+            a.record(st)
+            adm.round_plain(rounds)
+            b.record(st)
+            b.synchronize()
+            out["plain_dis_admm"] = a.elapsed_time(b) / 1e3 / rounds
+            out["mse_plain"] = float(np.mean((adm.get()[0].cpu().numpy() - L.x0) ** 2))
+        adm.close()
+    return {"workload": "lasso_small: A 128x256, 4 edge nodes, 1024-bit n, %d rounds" % rounds,
+            "s_per_iter_batched": out["batched"], "s_per_iter_per_node": out["per_node"],
+            "batched_speedup": out["per_node"] / out["batched"], "s_per_iter_plaintext_dis_admm": out["plain_dis_admm"],
+            "mse_private": out["mse"], "mse_plaintext": out["mse_plain"]}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -259,6 +320,7 @@ def run_gpu(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "cpu_baseline": cpu_base,
+        "admm": None if args.no_admm else run_admm(dev),
     }
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
@@ -288,6 +350,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pc2", choices=["pc2", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
     ap.add_argument("--groups", type=int, default=GROUPS)
     args = ap.parse_args()

@@ -56,6 +56,7 @@ struct pc2_admm {
   std::vector<int> off, tile_start;
   std::vector<long long> boffh;
   int ntiles = 0;
+  int mv_T = 1;  // lanes per row of the matvec (fixed at creation: it sets the row tiles)
   DevBuf<double> alpha, Bbar, x, z, v;
   DevBuf<uint32_t> bq, alpha_hat, zhat, vhat, shat, smont, xhat, D, round_ctr, bitlen;
   DevBuf<long long> boff, brow;
@@ -74,9 +75,8 @@ struct pc2_admm {
 
 namespace pc2 {
 
-template <int L2>
-static int matvec_launch(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
-  constexpr int T = lanes_for(L2);
+template <int L2, int T>
+static int matvec_launch_t(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
   if (!A->mvp) {
     std::shared_ptr<MatvecParams<L2>> p(new (std::nothrow) MatvecParams<L2>);
     if (!p) return PC2_ENOMEM;
@@ -94,6 +94,19 @@ static int matvec_launch(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
   if (!scr) return PC2_ENOMEM;
   return launch_matvec<L2, T>(P, A->alpha_hat.p, A->smont.p, A->bq.p, A->boff.p, A->node_off.p, A->tile_node.p + tile0,
                               A->tile_row0.p + tile0, A->xhat.p, scr, grid, st);
+}
+
+// Lanes per row of the matvec: the count picked at creation (built sets:
+// 1, 2, 4 for 16 limbs; 1, 2, 4, 8 for 32 and 64; 4, 8 for 128 and 192).
+template <int L2>
+static int matvec_launch(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
+  switch (A->mv_T) {
+    case 1: if constexpr (L2 <= 64) return matvec_launch_t<L2, 1>(A, tile0, ntl, st); break;
+    case 2: if constexpr (L2 <= 64) return matvec_launch_t<L2, 2>(A, tile0, ntl, st); break;
+    case 4: return matvec_launch_t<L2, 4>(A, tile0, ntl, st);
+    case 8: if constexpr (L2 >= 32) return matvec_launch_t<L2, 8>(A, tile0, ntl, st); break;
+  }
+  return PC2_EUNSUPPORTED;
 }
 
 template <int L2>
@@ -203,7 +216,10 @@ int pc2_admm_create(pc2_ctx* ctx, const pc2_key* key, const pc2_admm_params* prm
   A->qmax = std::rint((prm->zmax - prm->zmin) * A->scale);
   A->inv_s2 = std::ldexp(1.0, -2 * prm->log2_scale);
   // node layout and CTA row tiles (a tile never straddles two nodes)
-  const int G = kThreads / lanes_for(A->L2);
+  size_t Ntot = 0;
+  for (int k = 0; k < A->K; ++k) Ntot += prm->node_sizes[k] > 0 ? (size_t)prm->node_sizes[k] : 0;
+  A->mv_T = pick_config(ctx, OP_MATVEC, A->L2, Ntot).first;
+  const int G = kThreads / A->mv_T;
   A->off.assign(A->K + 1, 0);
   A->boffh.assign(A->K, 0);
   std::vector<int> nof, tnode, trow;

@@ -68,14 +68,21 @@ static uint32_t* ctx_scratch(void* c, size_t bytes) {
 
 uint32_t* ctx_scratch_get(pc2_ctx* ctx, size_t bytes) { return ctx_scratch(ctx, bytes); }
 
-// Lane counts built per operation and limb count (inst_crt_*.cu).
+// Lane counts built per operation and limb count (inst_crt_*.cu, inst_mv_*.cu).
 const int* lane_set(int op, int limbs, int* n) {
-  static const int s1[] = {1}, s124[] = {1, 2, 4}, s1248[] = {1, 2, 4, 8}, s248[] = {2, 4, 8};
-  (void)op;
-  switch (limbs) {
-    case 8: *n = 3; return s124;
-    case 16: case 32: case 64: *n = 4; return s1248;
-    case 96: *n = 3; return s248;
+  static const int s1[] = {1}, s124[] = {1, 2, 4}, s1248[] = {1, 2, 4, 8}, s248[] = {2, 4, 8}, s48[] = {4, 8};
+  if (op == OP_MATVEC) {
+    switch (limbs) {
+      case 16: *n = 3; return s124;
+      case 32: case 64: *n = 4; return s1248;
+      case 128: case 192: *n = 2; return s48;
+    }
+  } else {
+    switch (limbs) {
+      case 8: *n = 3; return s124;
+      case 16: case 32: case 64: *n = 4; return s1248;
+      case 96: *n = 3; return s248;
+    }
   }
   *n = 1;
   return s1;

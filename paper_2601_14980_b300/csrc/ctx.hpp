@@ -41,7 +41,7 @@ int hom_add_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* a, const uint32
 int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
                size_t base);
 
-enum { OP_ENC_CRT = 0, OP_DEC = 1 };
+enum { OP_ENC_CRT = 0, OP_DEC = 1, OP_MATVEC = 2 };
 
 // Lanes per element and window width (0 = key default) for `count` elements
 // of operation `op` on `limbs`-limb operands: the context's forced lane count,

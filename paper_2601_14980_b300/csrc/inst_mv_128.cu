@@ -1,0 +1,19 @@
+// inst_mv_128.cu -- encrypted matvec kernels for 128-limb n^2.
+#include "admm_kernels.cuh"
+
+namespace pc2 {
+
+template int launch_to_mont_rows<128, 4>(const ModConst<128>&, const uint32_t*, int, uint32_t*, int, cudaStream_t);
+template size_t matvec_scratch_words<128, 4>(int, int);
+template int launch_matvec<128, 4>(const MatvecParams<128>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                   const long long*, const int*, const int*, const int*, uint32_t*, uint32_t*, int,
+                                   cudaStream_t);
+template int matvec_grid<128, 4>(int, int);
+template int launch_to_mont_rows<128, 8>(const ModConst<128>&, const uint32_t*, int, uint32_t*, int, cudaStream_t);
+template size_t matvec_scratch_words<128, 8>(int, int);
+template int launch_matvec<128, 8>(const MatvecParams<128>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                   const long long*, const int*, const int*, const int*, uint32_t*, uint32_t*, int,
+                                   cudaStream_t);
+template int matvec_grid<128, 8>(int, int);
+
+}  // namespace pc2

@@ -1,0 +1,19 @@
+// inst_mv_192.cu -- encrypted matvec kernels for 192-limb n^2.
+#include "admm_kernels.cuh"
+
+namespace pc2 {
+
+template int launch_to_mont_rows<192, 4>(const ModConst<192>&, const uint32_t*, int, uint32_t*, int, cudaStream_t);
+template size_t matvec_scratch_words<192, 4>(int, int);
+template int launch_matvec<192, 4>(const MatvecParams<192>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                   const long long*, const int*, const int*, const int*, uint32_t*, uint32_t*, int,
+                                   cudaStream_t);
+template int matvec_grid<192, 4>(int, int);
+template int launch_to_mont_rows<192, 8>(const ModConst<192>&, const uint32_t*, int, uint32_t*, int, cudaStream_t);
+template size_t matvec_scratch_words<192, 8>(int, int);
+template int launch_matvec<192, 8>(const MatvecParams<192>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                   const long long*, const int*, const int*, const int*, uint32_t*, uint32_t*, int,
+                                   cudaStream_t);
+template int matvec_grid<192, 8>(int, int);
+
+}  // namespace pc2

@@ -141,3 +141,24 @@ def test_quantize_entry_point(env):
     assert ctx.status() == 0
     pc2.quantize(ctx, torch.tensor([9.0], dtype=torch.float64, device="cuda"), -8.0, 8.0, 24)
     assert ctx.status() & pc2.ST_QUANT
+
+
+@pytest.mark.parametrize("nbits,lanes", [(256, 1), (256, 4), (512, 2), (512, 8), (1024, 1), (1024, 4),
+                                         (2048, 2), (2048, 8), (3072, 4), (3072, 8)])
+def test_lanes_per_element_rounds_bit_exact(env, nbits, lanes):
+    """Every built lane count of the matvec (and of encryption/decryption where built) gives the oracle's iterates."""
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=4, M=24, N=40, nnz=4, K=3)   # nodes 14/13/13: ragged row tiles
+    pc2.set_lanes(ctx, lanes)
+    try:
+        st, kg, ko, adm = _make(env, L, nbits, seed=77)
+        ref = O.quantized_admm(st, L.lam, L.rho, 3, QP)
+        for t in range(3):
+            adm.round(1)
+            x, z, v, _ = adm.get()
+            assert np.array_equal(x.cpu().numpy(), ref.x[t]), (t, lanes)
+            assert np.array_equal(z.cpu().numpy(), ref.z[t]), (t, lanes)
+            assert np.array_equal(v.cpu().numpy(), ref.v[t]), (t, lanes)
+    finally:
+        pc2.set_lanes(ctx, 0)
+    assert ctx.status() == 0
