@@ -209,6 +209,67 @@ int pc2_admm_buffers(pc2_admm* admm, const uint32_t** zhat, const uint32_t** vha
 /* Bucket window c, windows per exponent, CTA row tiles of the matvec. */
 int pc2_admm_info(const pc2_admm* admm, int* c, int* nwin, int* ntiles);
 
+/* ---- batched rounds: many edge nodes, mixed key sizes ------------------ *
+ * The batching form of Algorithm 1: K edge nodes of uneven sizes, each node
+ * holding a key of one of up to five sizes (256 .. 3072-bit n; one key per
+ * size), every node's design block orthonormal (A_k^T A_k = I), so that
+ * B_k = I / (1 + rho), Bbar_k = rho / (1 + rho) I and Eq. (itq2) splits into
+ * 1 x 1 blocks.  Inputs: d_alpha = alpha_k = A_k^T y / (1 + rho) and d_bdiag =
+ * the diagonal of Bbar_k (N doubles each, node by node).  Element i of node k
+ * then runs, per round t: Gamma2(z_i), Gamma2(-v_i); z-hat_i, (-v)-hat_i =
+ * E_k(.) with r-streams (t << 8) | 1, (t << 8) | 2 and counter i (global
+ * index); x-hat_i = alpha-hat_i (+) b_i (x) (z-hat_i (+) (-v)-hat_i) with
+ * b_i = Gamma2(Bbar_ii); D_i = decrypt_k(x-hat_i); the exact decode with
+ * N_k = 1: x_i = fl(D_i + mS S + 2 mS b_i + mS (a_z + a_v) + 2 mS^2) / S^2;
+ * z_i = S_{lambda/rho}(v_i + x_i), v_i = v_i + x_i - z_i.  alpha-hat_i =
+ * E_k(Gamma1(alpha_i)) with r-stream 0.
+ * pc2_batch_round runs each round as ONE persistent launch over a work list
+ * of element tiles ordered longest first, captured once as a CUDA graph and
+ * replayed (a device round counter advances the r-streams); it uses constant
+ * memory of the library, so one batched round at a time may run per device.
+ * pc2_batch_round_per_node runs the same round node by node through the
+ * per-operation kernels (pc2_encrypt, pc2_hom_add, pc2_hom_scal,
+ * pc2_decrypt) and gives bit-identical state.  Status bits: PC2_ST_QUANT
+ * (a z or -v outside [zmin, zmax]), PC2_ST_RANGE (a decoded value outside
+ * 64 bits). */
+typedef struct {
+  int nodes;                  /* K */
+  const int* node_sizes;      /* host, K sizes N_k >= 1 */
+  const int* node_key;        /* host, K indices into keys[] */
+  int nkeys;
+  const pc2_key* const* keys; /* private keys, pairwise different sizes */
+  double lambda, rho;
+  double zmin, zmax;          /* public quantization range */
+  int log2_scale;             /* S = 2^log2_scale */
+  uint64_t seed;              /* Philox key of the encryption randomness */
+} pc2_batch_params;
+
+typedef struct pc2_batch pc2_batch;
+/* Quantizes and encrypts the inputs, builds the work list, x = z = v = 0,
+ * round 1.  Device buffers are owned by the object. */
+int pc2_batch_create(pc2_ctx* ctx, const pc2_batch_params* params, const double* d_alpha, const double* d_bdiag,
+                     pc2_batch** out, pc2_stream_t stream);
+void pc2_batch_destroy(pc2_batch* batch);
+/* x = z = v = 0, round 1 (synchronises `stream`). */
+int pc2_batch_reset(pc2_batch* batch, pc2_stream_t stream);
+/* `rounds` rounds, one persistent launch each (CUDA graph). */
+int pc2_batch_round(pc2_batch* batch, int rounds, pc2_stream_t stream);
+/* `rounds` rounds of the plain per-node path on the same state. */
+int pc2_batch_round_per_node(pc2_batch* batch, int rounds, pc2_stream_t stream);
+/* Copies x, z, v (device, N doubles each; any may be NULL) and the next round (host; synchronises). */
+int pc2_batch_get(pc2_batch* batch, double* d_x, double* d_z, double* d_v, uint32_t* h_round, pc2_stream_t stream);
+/* Device pointer of node `node`'s tiled ciphertexts of the last round
+ * (which: 0 alpha-hat, 1 z-hat, 2 (-v)-hat, 3 x-hat) and their limbs (2 L(n)). */
+int pc2_batch_ciphertexts(pc2_batch* batch, int which, int node, const uint32_t** d_tiled, int* limbs);
+/* Elements, work items, persistent grid and scratch bytes of the batched launch. */
+int pc2_batch_info(const pc2_batch* batch, size_t* elements, int* items, int* grid, size_t* scratch_bytes);
+/* Autotuner: times the window width (4..6) of each key's exponent schedules
+ * and the CTAs per SM (1..3) of the persistent launch on a sample of the work
+ * list (sample_items; 0 = one wave) without changing the state, and keeps the
+ * fastest.  h_result (optional, 6 ints): the window per key size (256, 512,
+ * 1024, 2048, 3072 bits; 0 = absent) and the CTAs per SM.  Synchronises. */
+int pc2_batch_tune(pc2_batch* batch, int sample_items, pc2_stream_t stream, int* h_result);
+
 /* ---- decryption without device allocation ---------------------------- *
  * Not from the paper (it has no counterpart there): a variant of pc2_decrypt
  * for callers that may not allocate device memory -- a process held to a

@@ -91,6 +91,18 @@ def dis_setup(A, y, sizes, rho) -> DisSetup:
     return DisSetup(sizes=list(sizes), offsets=offs, B=B, alpha=alpha, Bbar=Bbar)
 
 
+def diag_setup(aty, rho) -> DisSetup:
+    """Initialization of Sec. II for an orthonormal design (A^T A = I):
+    B = (I + rho I)^-1 = I / (1 + rho), alpha = B A^T y, Bbar = rho B, all
+    diagonal, written as 1 x 1 blocks (one per element) so that the per-node
+    products of Eq. (sldo091) / Eq. (itq2) reduce to their diagonal terms."""
+    aty = np.asarray(aty, dtype=np.float64)
+    N = len(aty)
+    Bk = np.array([[1.0 / (1.0 + rho)]])
+    return DisSetup(sizes=[1] * N, offsets=list(range(N + 1)), B=[Bk] * N,
+                    alpha=[np.array([a / (1.0 + rho)]) for a in aty], Bbar=[rho * Bk] * N)
+
+
 def dis_admm(setup: DisSetup, lam, rho, iters, jacobi: bool = False):
     """Distributed (plaintext) ADMM: Eq. (sldo091) per node, then Eqs. (ty32),
     (u78) at the master.  Returns (x, z, v) after `iters` rounds."""

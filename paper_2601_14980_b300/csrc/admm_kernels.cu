@@ -18,6 +18,7 @@
 //   k_zv_update    Eqs. (ty32), (u78) for the plaintext loop.
 #include <cuda_runtime.h>
 
+#include "admm_dev.cuh"
 #include "mont.cuh"
 #include "pc2_admm.h"
 #include "pc2_kernels.h"
@@ -25,16 +26,6 @@
 namespace pc2 {
 
 // ------------------------------------------------------------------ quantizer
-__device__ __forceinline__ uint64_t quant(double u, double zmin, double scale, double qmax, int* status) {
-  const double t = __dmul_rn(__dsub_rn(u, zmin), scale);
-  double r = rint(t);
-  if (!(r >= 0.0 && r <= qmax)) {  // also catches NaN
-    atomicOr(status, PC2_ST_QUANT);
-    r = r > qmax ? qmax : 0.0;
-  }
-  return (uint64_t)r;
-}
-
 __global__ void k_quantize(const double* __restrict__ u, size_t n, double zmin, double scale, double qmax, int negate,
                            uint64_t* __restrict__ q, int* status, uint32_t* bitlen_or) {
   uint32_t acc = 0;
@@ -64,13 +55,6 @@ __global__ void k_admm_quant(const double* __restrict__ z, const double* __restr
 }
 
 // ------------------------------------------------------------------ exact decode + z/v update
-__device__ __forceinline__ void zv_update(double x, double& z, double& v, double kappa) {
-  const double a = __dadd_rn(v, x);
-  const double zn = a > kappa ? __dsub_rn(a, kappa) : (a < -kappa ? __dadd_rn(a, kappa) : 0.0);
-  v = __dsub_rn(a, zn);
-  z = zn;
-}
-
 // D: decrypted plaintexts, tiled, Lh limbs; the quantized result must fit in
 // 128 bits (the upper words are checked to be zero).
 __global__ void k_admm_update(const uint32_t* __restrict__ D, int Lh, int N, const int* __restrict__ node_of,

@@ -425,3 +425,87 @@ def autotune(ctx: Context, key: Key, count: int, encrypt: bool = True, decrypt: 
     if decrypt:
         out["decrypt"] = (res[i], res[i + 1])
     return out
+
+
+class _BatchParams(ctypes.Structure):
+    _fields_ = [("nodes", _i), ("node_sizes", ctypes.POINTER(_i)), ("node_key", ctypes.POINTER(_i)),
+                ("nkeys", _i), ("keys", ctypes.POINTER(_vp)), ("lambda_", ctypes.c_double),
+                ("rho", ctypes.c_double), ("zmin", ctypes.c_double), ("zmax", ctypes.c_double),
+                ("log2_scale", _i), ("seed", _u64)]
+
+
+_batch_create = _sig("pc2_batch_create", [_vp, ctypes.POINTER(_BatchParams), _vp, _vp, ctypes.POINTER(_vp), _vp])
+_batch_destroy = _sig("pc2_batch_destroy", [_vp], None)
+_batch_reset = _sig("pc2_batch_reset", [_vp, _vp])
+_batch_round = _sig("pc2_batch_round", [_vp, _i, _vp])
+_batch_round_per_node = _sig("pc2_batch_round_per_node", [_vp, _i, _vp])
+_batch_get = _sig("pc2_batch_get", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32), _vp])
+_batch_ciphertexts = _sig("pc2_batch_ciphertexts", [_vp, _i, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)])
+_batch_info = _sig("pc2_batch_info", [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                      ctypes.POINTER(_sz)])
+_batch_tune = _sig("pc2_batch_tune", [_vp, _i, _vp, ctypes.POINTER(_i)])
+
+
+class Batch:
+    """Batched rounds over many edge nodes with mixed key sizes (see include/pc2.h)."""
+
+    def __init__(self, ctx: Context, keys, node_sizes, node_key, alpha, bdiag, lam: float, rho: float, zmin: float,
+                 zmax: float, log2_scale: int, seed: int, stream=None):
+        K = len(node_sizes)
+        self._sizes = (_i * K)(*[int(s) for s in node_sizes])
+        self._nkey = (_i * K)(*[int(s) for s in node_key])
+        self._keys = (_vp * len(keys))(*[k.h for k in keys])
+        p = _BatchParams(K, self._sizes, self._nkey, len(keys), self._keys, lam, rho, zmin, zmax, log2_scale, seed)
+        h = _vp()
+        _check(_batch_create(ctx.h, ctypes.byref(p), _ptr(alpha), _ptr(bdiag), ctypes.byref(h), _stream(stream)),
+               "pc2_batch_create")
+        self.h = h
+        self.N = int(sum(node_sizes))
+        self.ctx, self.keys = ctx, keys
+
+    def close(self):
+        if self.h:
+            _batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        _check(_batch_reset(self.h, _stream(stream)), "pc2_batch_reset")
+
+    def round(self, rounds: int = 1, stream=None):
+        _check(_batch_round(self.h, rounds, _stream(stream)), "pc2_batch_round")
+
+    def round_per_node(self, rounds: int = 1, stream=None):
+        _check(_batch_round_per_node(self.h, rounds, _stream(stream)), "pc2_batch_round_per_node")
+
+    def get(self, stream=None):
+        import torch
+
+        x, z, v = (torch.empty(self.N, dtype=torch.float64, device="cuda") for _ in range(3))
+        r = _u32()
+        _check(_batch_get(self.h, _ptr(x), _ptr(z), _ptr(v), ctypes.byref(r), _stream(stream)), "pc2_batch_get")
+        return x, z, v, r.value
+
+    def ciphertexts(self, which: str, node: int):
+        """(device pointer, limbs) of node `node`'s tiled ciphertexts: alpha_hat, zhat, vhat or xhat."""
+        p, limbs = _vp(), _i()
+        w = ["alpha_hat", "zhat", "vhat", "xhat"].index(which)
+        _check(_batch_ciphertexts(self.h, w, node, ctypes.byref(p), ctypes.byref(limbs)), "pc2_batch_ciphertexts")
+        return p.value, limbs.value
+
+    def info(self) -> dict:
+        n, it, g, sb = _sz(), _i(), _i(), _sz()
+        _check(_batch_info(self.h, ctypes.byref(n), ctypes.byref(it), ctypes.byref(g), ctypes.byref(sb)),
+               "pc2_batch_info")
+        return {"elements": n.value, "items": it.value, "grid": g.value, "scratch_bytes": sb.value}
+
+    def tune(self, sample_items: int = 0, stream=None) -> dict:
+        res = (_i * 6)()
+        _check(_batch_tune(self.h, sample_items, _stream(stream), res), "pc2_batch_tune")
+        return {"window": {b: res[i] for i, b in enumerate((256, 512, 1024, 2048, 3072)) if res[i]},
+                "ctas_per_sm": res[5]}

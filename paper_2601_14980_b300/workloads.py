@@ -16,6 +16,10 @@ Workloads (all seeded, all synthetic):
 * ``lasso_large``   -- 256x256 image-like signal (N = 65536) with 5% nonzero
   DCT-domain coefficients, A (N/4) x N with N(0, 4/N) entries, 16 nodes,
   3072-bit n, 50 iterations, lambda 0.005, rho 1.
+* ``batch_problem`` -- the batching form: 64 edge nodes with sizes
+  log-uniform in [256, 65536], keys of 1024/2048/3072 bits assigned to the
+  nodes in turn, an orthonormal design (A^T A = I), so only A^T y is drawn:
+  x0 with 5% N(0,1) nonzeros plus N(0, 0.01^2) noise.
 """
 from __future__ import annotations
 
@@ -108,3 +112,31 @@ def lasso_large(seed: int = 3, side: int = 256, frac: float = 0.05, K: int = 16,
     A = rng.standard_normal((M, N)) * np.sqrt(4.0 / N)
     y = A @ x0 + noise * rng.standard_normal(M)
     return Lasso(A=A, y=y, x0=x0, K=K, lam=lam, rho=rho, iters=iters)
+
+
+@dataclass
+class BatchProblem:
+    sizes: list          # N_k
+    node_key: list       # index into key_bits per node
+    key_bits: tuple
+    x0: np.ndarray
+    aty: np.ndarray      # A^T y, node by node (A^T A = I)
+    lam: float
+    rho: float
+
+
+def batch_problem(seed: int = 5, nodes: int = 64, lo: int = 256, hi: int = 65536,
+                  key_bits: tuple = (1024, 2048, 3072), frac: float = 0.05, noise: float = 0.01,
+                  lam: float = 0.01, rho: float = 1.0) -> BatchProblem:
+    """Edge-node sizes log-uniform in [lo, hi]; node k holds key key_bits[k % len].
+    With orthonormal columns, A^T y = x0 + A^T w and A^T w ~ N(0, noise^2 I)."""
+    rng = np.random.default_rng(seed)
+    sizes = [int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi)))))) for _ in range(nodes)]
+    N = sum(sizes)
+    x0 = np.zeros(N)
+    nnz = max(1, int(round(frac * N)))
+    pos = rng.choice(N, size=nnz, replace=False)
+    x0[pos] = rng.standard_normal(nnz)
+    aty = x0 + noise * rng.standard_normal(N)
+    return BatchProblem(sizes=sizes, node_key=[k % len(key_bits) for k in range(nodes)], key_bits=tuple(key_bits),
+                        x0=x0, aty=aty, lam=lam, rho=rho)

@@ -181,3 +181,51 @@ def test_quantization_error_bound_and_mse():
     mse_priv = np.mean((qz.x[-1] - L.x0) ** 2)
     mse_plain = np.mean((xs[-1] - L.x0) ** 2)
     assert abs(mse_priv - mse_plain) <= (2 * np.linalg.norm(xs[-1] - L.x0) * dT + dT ** 2) / 24
+
+
+def test_diag_setup_is_the_orthonormal_closed_form():
+    """diag_setup equals the general initialization (B_k = (A_k^T A_k + rho I)^-1)
+    for an orthonormal design, and its Dis-ADMM reaches the LASSO closed form."""
+    rng = np.random.default_rng(3)
+    M, sizes, rho, lam = 80, [7, 20, 13], 1.0, 0.05
+    N = sum(sizes)
+    A, _ = np.linalg.qr(rng.standard_normal((M, N)))
+    y = rng.standard_normal(M)
+    full = O.dis_setup(A, y, sizes, rho)
+    diag = O.diag_setup(A.T @ y, rho)
+    alpha_full = np.concatenate(full.alpha)
+    alpha_diag = np.array([a[0] for a in diag.alpha])
+    assert np.allclose(alpha_full, alpha_diag, atol=1e-14)
+    for k, Bb in enumerate(full.Bbar):
+        o = full.offsets[k]
+        assert np.allclose(Bb, np.diag([diag.Bbar[o + i][0, 0] for i in range(sizes[k])]), atol=1e-14)
+    x, z, v = O.dis_admm(diag, lam, rho, 300)
+    assert np.allclose(z, O.soft_threshold(A.T @ y, lam), atol=1e-9)
+
+
+def test_one_by_one_blocks_equal_diagonal_node_blocks_exactly():
+    """With a diagonal Bbar_k the quantized round over N_k x N_k node blocks and
+    over 1 x 1 blocks give identical iterates: the off-diagonal b_ij = Gamma2(0)
+    dequantize to exactly zero in the exact decode."""
+    rng = np.random.default_rng(4)
+    sizes, rho, lam = [5, 9, 4], 1.0, 0.02
+    aty = rng.standard_normal(sum(sizes))
+    qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+    diag = O.diag_setup(aty, rho)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(int).tolist()
+    blocks = O.DisSetup(sizes=sizes, offsets=offs,
+                        B=[np.eye(n) / (1 + rho) for n in sizes],
+                        alpha=[np.array([diag.alpha[i][0] for i in range(offs[k], offs[k + 1])])
+                               for k in range(len(sizes))],
+                        Bbar=[np.diag([diag.Bbar[i][0, 0] for i in range(offs[k], offs[k + 1])])
+                              for k in range(len(sizes))])
+    a = O.quantized_admm(diag, lam, rho, 4, qp)
+    b = O.quantized_admm(blocks, lam, rho, 4, qp)
+    for t in range(4):
+        assert np.array_equal(a.x[t], b.x[t]) and np.array_equal(a.z[t], b.z[t]) and np.array_equal(a.v[t], b.v[t])
+
+
+def test_batch_problem_shape():
+    bp = W.batch_problem(seed=1, nodes=10, lo=8, hi=100)
+    assert len(bp.sizes) == 10 and all(8 <= s <= 100 for s in bp.sizes)
+    assert len(bp.aty) == sum(bp.sizes) and bp.node_key[:4] == [0, 1, 2, 0]
