@@ -270,6 +270,57 @@ int pc2_batch_info(const pc2_batch* batch, size_t* elements, int* items, int* gr
  * 1024, 2048, 3072 bits; 0 = absent) and the CTAs per SM.  Synchronises. */
 int pc2_batch_tune(pc2_batch* batch, int sample_items, pc2_stream_t stream, int* h_result);
 
+/* ---- serving: a request loop with continuous batching ------------------ *
+ * A server owns one private key (512 or 2048-bit n) and a device arena for
+ * the requests' buffers.  Callers (any thread) submit encrypt, decrypt and
+ * aggregate requests with HOST buffers, which must stay valid (and, for
+ * asynchronous copies, should be page-locked) until pc2_server_wait returns.
+ *   PC2_OP_ENCRYPT   in: count uint64 plaintexts; out: tiled ciphertexts
+ *                    (2 L(n) limbs); the result equals pc2_encrypt(.., seed,
+ *                    stream, e0, ..) (key-owner CRT path).
+ *   PC2_OP_DECRYPT   in: tiled ciphertexts; out: tiled plaintexts (L(n) limbs),
+ *                    equal to pc2_decrypt.
+ *   PC2_OP_AGGREGATE in: `groups` (2..32) tiled ciphertext arrays of `count`
+ *                    elements back to back (pc2_tiled_words(count, 2 L(n))
+ *                    words each); out: their product mod n^2, equal to
+ *                    pc2_hom_sum.
+ * Mode 0 (continuous batching): a worker thread admits requests in arrival
+ * order as arena space frees up (first fit; at most max_active at once),
+ * copies their inputs in, and runs steps, each ONE persistent launch over
+ * work items of every admitted request (elements of requests of at most
+ * small_request elements get 8 lanes each, others one; a step holds about
+ * step_budget one-lane encryption items per CTA); two steps are in flight,
+ * so requests that arrive while others run join the next step and their work
+ * overlaps on the device.  Mode 1 (the plain per-request path): requests run
+ * one at a time, in arrival order, through pc2_encrypt / pc2_decrypt /
+ * pc2_hom_sum on the context (do not use that context from other threads
+ * meanwhile).  Results are identical in both modes and do not depend on what
+ * else runs.  Servers of the same key size share a constant-memory block: at
+ * most one of them may have requests in flight at a time. */
+enum { PC2_OP_ENCRYPT = 1, PC2_OP_DECRYPT = 2, PC2_OP_AGGREGATE = 3 };
+typedef struct {
+  size_t arena_bytes;    /* device bytes for the requests' buffers (admission limit) */
+  int mode;              /* 0: continuous batching; 1: plain per-request path */
+  int max_active;        /* requests admitted at once (0: 256) */
+  size_t small_request;  /* requests of at most this many elements get 8 lanes per element (0: 4096) */
+  double step_budget;    /* work per CTA and step, in one-lane encryption items (0: 1.0) */
+} pc2_server_params;
+
+typedef struct pc2_server pc2_server;
+int pc2_server_create(pc2_ctx* ctx, const pc2_key* key, const pc2_server_params* params, pc2_server** out);
+/* Finishes the requests already submitted, then frees everything. */
+void pc2_server_destroy(pc2_server* server);
+/* Queues a request; *ticket identifies it.  PC2_ENOMEM when its buffers can
+ * never fit the arena. */
+int pc2_server_submit(pc2_server* server, int op, const void* h_in, size_t count, int groups, uint64_t seed,
+                      uint32_t stream, uint64_t e0, void* h_out, uint64_t* ticket);
+/* Blocks until the request is done (its output is in h_out) or timeout_s
+ * passes (PC2_ETIMEOUT; the ticket stays valid).  latency_s: submit to done.
+ * Returns the request's status and forgets the ticket. */
+int pc2_server_wait(pc2_server* server, uint64_t ticket, double timeout_s, double* latency_s);
+/* Requests completed, steps launched, work items run, peak arena bytes in use. */
+int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, uint64_t* items, size_t* arena_peak);
+
 /* ---- decryption without device allocation ---------------------------- *
  * Not from the paper (it has no counterpart there): a variant of pc2_decrypt
  * for callers that may not allocate device memory -- a process held to a

@@ -24,7 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "admm_dev.cuh"
-#include "paillier_kernels.cuh"
+#include "crt_dev.cuh"
 #include "pc2_batch.h"
 
 namespace pc2 {
@@ -40,94 +40,6 @@ __device__ __forceinline__ const uint32_t* bmod() {
   else if constexpr (Lh == 64) return c_bmods.m64[H];
   else return nullptr;
 }
-
-// GM = 1 + m n for a 64-bit m (zero-padded to `total` words); M: temporary column.
-__device__ __forceinline__ void gm_u64(const Col& GM, const Col& M, uint64_t m, const uint32_t* n, int Ln, int total) {
-  M[0] = (uint32_t)m;
-  M[1] = (uint32_t)(m >> 32);
-  g_mul(GM, M, 2, PArr{n}, Ln);
-  uint64_t c = 1;
-  for (int j = 0; j < 2 + Ln; ++j) {
-    c += GM[j];
-    GM[j] = (uint32_t)c;
-    c >>= 32;
-  }
-  for (int j = 2 + Ln; j < total; ++j) GM[j] = 0u;
-}
-
-// One CRT half of an encryption: OUT = r^n (1 + m n) mod h^2 (h^2 = Mg.n).
-template <int Lh, int T, int H>
-__device__ __forceinline__ void enc_half_b(const ModConst<Lh>& Mg, const Sched<kMaxSched>& E, const Col& X,
-                                           const Col& GM, const Col& OUT, const Col& A, const Col& B, const Col& C,
-                                           const Col& TT, const Col& tab, const Col& bsh, const Grp<T>& g) {
-  constexpr int S = Lh / T;
-  const uint32_t np = Mg.np;
-  g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // r R mod h^2
-  __syncwarp();
-  uint32_t a[S];
-  load_seg(a, A, g);
-  if constexpr (T == 1) run_modexp<S, T>(a, E, bmod<Lh, H>(), np, tab, bsh, g);
-  else run_modexp<S, T>(a, E, Mg.n, np, tab, bsh, g);      // (r^n mod h^2) R
-  store_seg(A, a, g);
-  __syncwarp();
-  g_to_mont_2l(B, GM, Mg.n, Mg.r2, Mg.r3, np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
-  g_mont(C, A, B, Mg.n, np, Lh, TT);
-  g_zero(B, Lh);
-  B[0] = 1u;
-  g_mont(OUT, C, B, Mg.n, np, Lh, TT);
-}
-
-// One CRT half of a decryption: OUT = L_h(c^(h-1) mod h^2) h_h mod h.
-template <int Lh, int T, int H>
-__device__ __forceinline__ void dec_half_b(const ModConst<Lh>& Mg, const Sched<kMaxSchedHalf>& E, const uint32_t* h,
-                                           uint32_t hnp, const uint32_t* hinvlo, const uint32_t* hhR, const Col& X,
-                                           const Col& OUT, const Col& A, const Col& B, const Col& C, const Col& TT,
-                                           const Col& tab, const Col& bsh, const Grp<T>& g) {
-  constexpr int S = Lh / T, Lp = Lh / 2;
-  const uint32_t np = Mg.np;
-  g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // c R mod h^2
-  __syncwarp();
-  uint32_t a[S];
-  load_seg(a, A, g);
-  if constexpr (T == 1) run_modexp<S, T>(a, E, bmod<Lh, H>(), np, tab, bsh, g);
-  else run_modexp<S, T>(a, E, Mg.n, np, tab, bsh, g);      // c^(h-1) R mod h^2
-  store_seg(A, a, g);
-  __syncwarp();
-  g_zero(B, Lh);
-  B[0] = 1u;
-  g_mont(C, A, B, Mg.n, np, Lh, TT);  // x = c^(h-1) mod h^2 = 1 mod h
-  {
-    uint64_t br = 1;
-    for (int j = 0; j < Lh && br; ++j) {
-      const uint32_t v = C[j];
-      C[j] = v - 1u;
-      br = (v == 0u);
-    }
-  }
-  g_mul_lo(A, C, PArr{hinvlo}, Lp);  // (x - 1) / h exactly
-  g_copy_param(B, hhR, Lp);
-  g_mont(OUT, A, B, h, hnp, Lp, TT);
-}
-
-// acc = base^k in Montgomery form (base given as x R), fixed windows of w
-// bits over nd digits (warp-uniform); tab: 2^w entries of len words.
-__device__ __forceinline__ void g_pow_u64(const Col& acc, const Col& base, uint64_t k, int w, int nd, const Col& tab,
-                                          const uint32_t* r1, const uint32_t* N, uint32_t np, int len,
-                                          const Col& tt) {
-  const int ntab = 1 << w;
-  const uint64_t mask = (uint64_t)ntab - 1u;
-  g_copy_param(tab, r1, len);
-  g_copy(tab.off(len), base, len);
-  for (int d = 2; d < ntab; ++d) g_mont(tab.off(d * len), tab.off((d - 1) * len), tab.off(len), N, np, len, tt);
-  int pos = nd - 1;
-  g_copy(acc, tab.off((int)((k >> (pos * w)) & mask) * len), len);
-  for (--pos; pos >= 0; --pos) {
-    for (int s = 0; s < w; ++s) g_mont(acc, acc, acc, N, np, len, tt);
-    g_mont(acc, acc, tab.off((int)((k >> (pos * w)) & mask) * len), N, np, len, tt);
-  }
-}
-
-constexpr int kScalWin = 4;  // window of the scaling exponent b_i (< 2^32)
 
 template <int Lh, int T>
 __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem& I, uint32_t round, uint32_t* cta,
@@ -162,8 +74,8 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
     const uint32_t sid = (round << 8) | (which ? 2u : 1u);
     gen_r(X, P.seed, sid, e, Lh + 2, L2);
     gm_u64(GM, A, which ? qv : qz, K.enc.nwords, Lh, L2);
-    enc_half_b<Lh, T, 0>(K.enc.mp, K.enc.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
-    enc_half_b<Lh, T, 1>(K.enc.mq, K.enc.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
+    enc_half_f<Lh, T>(K.enc.mp, bmod<Lh, 0>(), K.enc.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
+    enc_half_f<Lh, T>(K.enc.mq, bmod<Lh, 1>(), K.enc.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
     g_copy_param(B, K.enc.pinv2R, Lh);
@@ -197,9 +109,9 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
   __syncwarp();
 
   // D = decrypt(x-hat): CRT halves, Garner m = m_p + p [(m_q - m_p) p^-1 mod q]
-  dec_half_b<Lh, T, 0>(K.dec.mp, K.dec.ep, K.dec.p, K.dec.pnp, K.dec.pinvlo, K.dec.hpR, X, CP, A, B, C, TT, tab, bsh,
+  dec_half_f<Lh, T>(K.dec.mp, bmod<Lh, 0>(), K.dec.ep, K.dec.p, K.dec.pnp, K.dec.pinvlo, K.dec.hpR, X, CP, A, B, C, TT, tab, bsh,
                        g);
-  dec_half_b<Lh, T, 1>(K.dec.mq, K.dec.eq, K.dec.q, K.dec.qnp, K.dec.qinvlo, K.dec.hqR, X, CQ, A, B, C, TT, tab, bsh,
+  dec_half_f<Lh, T>(K.dec.mq, bmod<Lh, 1>(), K.dec.eq, K.dec.q, K.dec.qnp, K.dec.qinvlo, K.dec.hqR, X, CQ, A, B, C, TT, tab, bsh,
                        g);
   if (g_sub(A, CQ, CP, Lp)) g_add(A, A, PArr{K.dec.q}, Lp);
   g_copy_param(B, K.dec.pinvqR, Lp);

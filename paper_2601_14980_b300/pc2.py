@@ -509,3 +509,66 @@ class Batch:
         _check(_batch_tune(self.h, sample_items, _stream(stream), res), "pc2_batch_tune")
         return {"window": {b: res[i] for i, b in enumerate((256, 512, 1024, 2048, 3072)) if res[i]},
                 "ctas_per_sm": res[5]}
+
+
+class _ServerParams(ctypes.Structure):
+    _fields_ = [("arena_bytes", _sz), ("mode", _i), ("max_active", _i), ("small_request", _sz),
+                ("step_budget", ctypes.c_double)]
+
+
+_server_create = _sig("pc2_server_create", [_vp, _vp, ctypes.POINTER(_ServerParams), ctypes.POINTER(_vp)])
+_server_destroy = _sig("pc2_server_destroy", [_vp], None)
+_server_submit = _sig("pc2_server_submit", [_vp, _i, _vp, _sz, _i, _u64, _u32, _u64, _vp, ctypes.POINTER(_u64)])
+_server_wait = _sig("pc2_server_wait", [_vp, _u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)])
+_server_stats = _sig("pc2_server_stats", [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                          ctypes.POINTER(_sz)])
+
+OP_ENCRYPT, OP_DECRYPT, OP_AGGREGATE = 1, 2, 3
+
+
+class Server:
+    """Request loop with continuous batching (mode 0) or the plain per-request path (mode 1)."""
+
+    def __init__(self, ctx: Context, key: Key, arena_bytes: int, mode: int = 0, max_active: int = 0,
+                 small_request: int = 0, step_budget: float = 0.0):
+        p = _ServerParams(arena_bytes, mode, max_active, small_request, step_budget)
+        h = _vp()
+        _check(_server_create(ctx.h, key.h, ctypes.byref(p), ctypes.byref(h)), "pc2_server_create")
+        self.h = h
+        self.key = key
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            _server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, op: int, h_in, count: int, h_out, groups: int = 1, seed: int = 0, stream: int = 0,
+               e0: int = 0) -> int:
+        """h_in / h_out: host torch tensors (page-locked for overlap), kept alive until wait()."""
+        t = _u64()
+        _check(_server_submit(self.h, op, h_in.data_ptr(), count, groups, seed, stream, e0, h_out.data_ptr(),
+                              ctypes.byref(t)), "pc2_server_submit")
+        self._keep[t.value] = (h_in, h_out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 600.0) -> float:
+        lat = ctypes.c_double()
+        rc = _server_wait(self.h, ticket, timeout, ctypes.byref(lat))
+        if rc != -6:  # PC2_ETIMEOUT keeps the ticket
+            self._keep.pop(ticket, None)
+        _check(rc, "pc2_server_wait")
+        return lat.value
+
+    def stats(self) -> dict:
+        c, s, i, a = _u64(), _u64(), _u64(), _sz()
+        _check(_server_stats(self.h, ctypes.byref(c), ctypes.byref(s), ctypes.byref(i), ctypes.byref(a)),
+               "pc2_server_stats")
+        return {"completed": c.value, "steps": s.value, "items": i.value, "arena_peak": a.value}
