@@ -247,6 +247,76 @@ def run_batch(dev, rounds: int = 1, per_node_rounds: int = 1, tune: bool = True)
             "status": status, "clocks": clocks}
 
 
+def run_serve(dev, rates=(5.0, 15.0, 30.0, 45.0, 60.0), seconds: float = 4.0, seed: int = 11):
+    """Serving form: Poisson arrivals of encrypt / decrypt / aggregate requests
+    (one third each) from 256 simulated edge nodes, 2048-bit n, sizes
+    log-uniform in [64, 32768] ciphertexts, aggregates of 2..16 node vectors,
+    payloads rint(N(0,1) 2^24) + 2^47; device-resident key and request buffers
+    with memory admission.  p50/p99 latency and ciphertexts/s per arrival rate
+    for continuous batching (mode 0) and the plain per-request path (mode 1)."""
+    import numpy as np
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+    from paper_2601_14980_b300 import workloads as W
+
+    ctx = pc2.Context(dev)
+    key = pc2.Key.generate(2048, 2027)
+    L, L2 = key.limbs, 2 * key.limbs
+    MAXC, GMAX = 32768, 16
+    m = W.plaintexts_u64(MAXC, seed=seed)
+    h_m = torch.from_numpy(m.view(np.int64)).pin_memory()
+    dm = h_m.to(dev)
+    stride = pc2.tiled_words(MAXC, L2)
+    pool = torch.empty(GMAX * stride, dtype=torch.int32, device=dev)
+    for g in range(GMAX):
+        pc2.encrypt(ctx, key, dm, seed, 1000 + g, 0, out=pool[g * stride:(g + 1) * stride])
+    h_pool = pool.cpu().pin_memory()
+    del pool
+    rng = np.random.default_rng(seed)
+    points = []
+    for rate in rates:
+        n = max(20, int(rate * seconds))
+        arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        ops = rng.integers(1, 4, n)
+        counts = np.exp(rng.uniform(np.log(64), np.log(MAXC), n)).astype(int)
+        groups = rng.integers(2, GMAX + 1, n)
+        nodes = rng.integers(0, 256, n)
+        outw = [pc2.tiled_words(int(c), L if o == pc2.OP_DECRYPT else L2) for o, c in zip(ops, counts)]
+        offs = np.concatenate([[0], np.cumsum(outw)]).astype(int)
+        h_out = torch.empty(int(offs[-1]), dtype=torch.int32).pin_memory()
+        res = {"rate_per_s": rate, "requests": n, "ciphertexts": int(counts.sum())}
+        for mode, name in ((0, "batched"), (1, "per_request")):
+            srv = pc2.Server(ctx, key, arena_bytes=4 << 30, mode=mode)
+            t0 = time.perf_counter()
+            tickets, sub = [], []
+            for i in range(n):
+                d = t0 + arr[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                o, c = int(ops[i]), int(counts[i])
+                out = h_out[offs[i]:offs[i + 1]]
+                if o == pc2.OP_ENCRYPT:
+                    h_in = h_m
+                elif o == pc2.OP_DECRYPT:
+                    h_in = h_pool
+                else:
+                    h_in = h_pool
+                sub.append(time.perf_counter())
+                tickets.append(srv.submit(o, h_in, c, out, groups=int(groups[i]), seed=seed, stream=int(nodes[i]),
+                                          e0=int(rng.integers(0, 1 << 20)), h_stride=stride))
+            lats = [srv.wait(t) for t in tickets]
+            span = max(s + l for s, l in zip(sub, lats)) - t0
+            st = srv.stats()
+            srv.close()
+            res[name] = {"p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
+                         "ciphertexts_per_s": int(counts.sum()) / span, "makespan_s": span, "steps": st["steps"]}
+        points.append(res)
+    return {"workload": "serving: Poisson arrivals from 256 edge nodes, 2048-bit n, sizes log-uniform [64, 32768], "
+                        "encrypt/decrypt/aggregate(2..16) in equal shares, %.0f s per rate" % seconds,
+            "points": points, "status": ctx.status()}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -377,6 +447,7 @@ def run_gpu(args):
         "cpu_baseline": cpu_base,
         "admm": None if args.no_admm else run_admm(dev),
         "batch": None if args.no_batch else run_batch(dev, args.batch_rounds),
+        "serve": None if args.no_serve else run_serve(dev),
     }
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
@@ -408,6 +479,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
     ap.add_argument("--groups", type=int, default=GROUPS)

@@ -281,9 +281,10 @@ int pc2_batch_tune(pc2_batch* batch, int sample_items, pc2_stream_t stream, int*
  *   PC2_OP_DECRYPT   in: tiled ciphertexts; out: tiled plaintexts (L(n) limbs),
  *                    equal to pc2_decrypt.
  *   PC2_OP_AGGREGATE in: `groups` (2..32) tiled ciphertext arrays of `count`
- *                    elements back to back (pc2_tiled_words(count, 2 L(n))
- *                    words each); out: their product mod n^2, equal to
- *                    pc2_hom_sum.
+ *                    elements, h_stride words apart (0: back to back,
+ *                    pc2_tiled_words(count, 2 L(n)) words; a larger stride
+ *                    takes the first `count` elements of longer arrays);
+ *                    out: their product mod n^2, equal to pc2_hom_sum.
  * Mode 0 (continuous batching): a worker thread admits requests in arrival
  * order as arena space frees up (first fit; at most max_active at once),
  * copies their inputs in, and runs steps, each ONE persistent launch over
@@ -312,8 +313,8 @@ int pc2_server_create(pc2_ctx* ctx, const pc2_key* key, const pc2_server_params*
 void pc2_server_destroy(pc2_server* server);
 /* Queues a request; *ticket identifies it.  PC2_ENOMEM when its buffers can
  * never fit the arena. */
-int pc2_server_submit(pc2_server* server, int op, const void* h_in, size_t count, int groups, uint64_t seed,
-                      uint32_t stream, uint64_t e0, void* h_out, uint64_t* ticket);
+int pc2_server_submit(pc2_server* server, int op, const void* h_in, size_t count, int groups, size_t h_stride,
+                      uint64_t seed, uint32_t stream, uint64_t e0, void* h_out, uint64_t* ticket);
 /* Blocks until the request is done (its output is in h_out) or timeout_s
  * passes (PC2_ETIMEOUT; the ticket stays valid).  latency_s: submit to done.
  * Returns the request's status and forgets the ticket. */

@@ -103,6 +103,7 @@ struct Req {
   const void* h_in = nullptr;
   void* h_out = nullptr;
   size_t in_bytes = 0, out_bytes = 0, ct_stride = 0;
+  size_t h_stride = 0;      // aggregate: words between the group arrays in h_in
   size_t in_off = 0, out_off = 0;
   size_t cursor = 0;        // next element to schedule
   size_t outstanding = 0;   // scheduled items not yet finished
@@ -443,9 +444,18 @@ static void worker_main(pc2_server* S) {
         }
         r->in_off = io;
         r->out_off = oo;
-        if (cudaMemcpyAsync(S->arena_mem + io, r->h_in, r->in_bytes, cudaMemcpyHostToDevice, S->copy_in) !=
-                cudaSuccess ||
-            cudaEventRecord(r->h2d, S->copy_in) != cudaSuccess) {
+        // inputs in; aggregate operands packed group by group (ct_stride words apart)
+        bool ok = true;
+        if (r->op == PC2_OP_AGGREGATE) {
+          for (int gi = 0; gi < r->groups && ok; ++gi)
+            ok = cudaMemcpyAsync(S->arena_mem + io + (size_t)gi * r->ct_stride * 4,
+                                 static_cast<const uint32_t*>(r->h_in) + (size_t)gi * r->h_stride, r->ct_stride * 4,
+                                 cudaMemcpyHostToDevice, S->copy_in) == cudaSuccess;
+        } else {
+          ok = cudaMemcpyAsync(S->arena_mem + io, r->h_in, r->in_bytes, cudaMemcpyHostToDevice, S->copy_in) ==
+               cudaSuccess;
+        }
+        if (!ok || cudaEventRecord(r->h2d, S->copy_in) != cudaSuccess) {
           lk.unlock();
           return fail_all(S, PC2_ECUDA);
         }
@@ -574,8 +584,8 @@ void pc2_server_destroy(pc2_server* S) {
   delete S;
 }
 
-int pc2_server_submit(pc2_server* S, int op, const void* h_in, size_t count, int groups, uint64_t seed,
-                      uint32_t stream, uint64_t e0, void* h_out, uint64_t* ticket) {
+int pc2_server_submit(pc2_server* S, int op, const void* h_in, size_t count, int groups, size_t h_stride,
+                      uint64_t seed, uint32_t stream, uint64_t e0, void* h_out, uint64_t* ticket) {
   if (!S || !h_in || !h_out || !ticket || !count || op < PC2_OP_ENCRYPT || op > PC2_OP_AGGREGATE) return PC2_EINVAL;
   if (op == PC2_OP_AGGREGATE && (groups < 2 || groups > kMaxGroups)) return PC2_EINVAL;
   auto r = std::make_shared<Req>();
@@ -589,6 +599,8 @@ int pc2_server_submit(pc2_server* S, int op, const void* h_in, size_t count, int
   r->h_out = h_out;
   const int L2 = 2 * S->Lh;
   r->ct_stride = pc2_tiled_words(count, L2);
+  r->h_stride = h_stride ? h_stride : r->ct_stride;
+  if (op == PC2_OP_AGGREGATE && r->h_stride < r->ct_stride) return PC2_EINVAL;
   if (op == PC2_OP_ENCRYPT) {
     r->in_bytes = count * 8;
     r->out_bytes = r->ct_stride * 4;

@@ -518,7 +518,7 @@ class _ServerParams(ctypes.Structure):
 
 _server_create = _sig("pc2_server_create", [_vp, _vp, ctypes.POINTER(_ServerParams), ctypes.POINTER(_vp)])
 _server_destroy = _sig("pc2_server_destroy", [_vp], None)
-_server_submit = _sig("pc2_server_submit", [_vp, _i, _vp, _sz, _i, _u64, _u32, _u64, _vp, ctypes.POINTER(_u64)])
+_server_submit = _sig("pc2_server_submit", [_vp, _i, _vp, _sz, _i, _sz, _u64, _u32, _u64, _vp, ctypes.POINTER(_u64)])
 _server_wait = _sig("pc2_server_wait", [_vp, _u64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)])
 _server_stats = _sig("pc2_server_stats", [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
                                           ctypes.POINTER(_sz)])
@@ -551,11 +551,11 @@ class Server:
             pass
 
     def submit(self, op: int, h_in, count: int, h_out, groups: int = 1, seed: int = 0, stream: int = 0,
-               e0: int = 0) -> int:
+               e0: int = 0, h_stride: int = 0) -> int:
         """h_in / h_out: host torch tensors (page-locked for overlap), kept alive until wait()."""
         t = _u64()
-        _check(_server_submit(self.h, op, h_in.data_ptr(), count, groups, seed, stream, e0, h_out.data_ptr(),
-                              ctypes.byref(t)), "pc2_server_submit")
+        _check(_server_submit(self.h, op, h_in.data_ptr(), count, groups, h_stride, seed, stream, e0,
+                              h_out.data_ptr(), ctypes.byref(t)), "pc2_server_submit")
         self._keep[t.value] = (h_in, h_out)
         return t.value
 

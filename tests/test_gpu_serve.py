@@ -161,3 +161,22 @@ def test_rejects_what_cannot_fit(env):
     with pytest.raises(pc2.Pc2Error):
         srv.submit(pc2.OP_AGGREGATE, h_in, 10, h_out, groups=1)
     srv.close()
+
+
+def test_aggregate_from_a_strided_pool(env):
+    torch, pc2, ctx = env
+    kg, _ = _keys(pc2, 512)
+    L2 = 2 * kg.limbs
+    m = W.plaintexts_u64(500, seed=5)
+    dm = torch.from_numpy(m.view(np.int64)).cuda()
+    pool = torch.cat([pc2.encrypt(ctx, kg, dm, SEED + g, g, 0)[:pc2.tiled_words(500, L2)] for g in range(3)])
+    stride = pc2.tiled_words(500, L2)
+    count = 100
+    packed = torch.cat([pool[g * stride:g * stride + pc2.tiled_words(count, L2)] for g in range(3)])
+    want = pc2.unpack(ctx, pc2.hom_sum(ctx, kg, packed, 3, count), count, L2).cpu()
+    h_in = pool.cpu().pin_memory()
+    h_out = torch.zeros(pc2.tiled_words(count, L2), dtype=torch.int32).pin_memory()
+    srv = pc2.Server(ctx, kg, arena_bytes=16 << 20)
+    srv.wait(srv.submit(pc2.OP_AGGREGATE, h_in, count, h_out, groups=3, h_stride=stride))
+    srv.close()
+    assert torch.equal(pc2.unpack(ctx, h_out.cuda(), count, L2).cpu(), want)
