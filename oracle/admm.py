@@ -210,6 +210,27 @@ class PrivateTrace:
     vhat: list = field(default_factory=list)
 
 
+def exact_rowdot(b, a) -> list:
+    """Exact integers sum_j b_ij a_j for every row i of a non-negative int64
+    matrix b (entries < 2^31) and non-negative ints a_j (< 2^31).
+
+    Small problems use Python integers term by term.  Large ones split
+    a_j = a_hi 2^16 + a_lo and take two int64 matrix-vector products (numpy,
+    no floating point): every term b_ij a_lo < 2^47 and b_ij a_hi < 2^46, so
+    both sums stay below 2^63 for rows of up to 2^15 terms; the two exact sums
+    are recombined as Python integers."""
+    b = np.asarray(b, dtype=np.int64)
+    n = b.shape[1] if b.ndim == 2 else 0
+    if b.size <= 1 << 16:
+        return [sum(int(b[i, j]) * int(a[j]) for j in range(n)) for i in range(b.shape[0])]
+    if n > 1 << 15 or np.any(b < 0) or np.any(b >= 1 << 31) or any(x < 0 or x >= 1 << 31 for x in a):
+        raise ValueError("exact_rowdot: operand outside the split's range")
+    av = np.asarray(a, dtype=np.int64)
+    lo = b @ (av & 0xFFFF)
+    hi = b @ (av >> 16)
+    return [(int(h) << 16) + int(l) for h, l in zip(hi, lo)]
+
+
 def _quantized_setup(setup: DisSetup, qp: QParams):
     c = [gamma1(a, qp) for a in setup.alpha]
     b = [gamma2(Bb, qp) for Bb in setup.Bbar]
@@ -232,8 +253,7 @@ def quantized_admm(setup: DisSetup, lam, rho, iters, qp: QParams) -> PrivateTrac
         Dall = []
         for k, (a0, a1) in enumerate(zip(setup.offsets[:-1], setup.offsets[1:])):
             a = [int(zq[j]) + int(vq[j]) for j in range(a0, a1)]
-            bk = b[k]
-            D = [int(c[k][i]) + sum(int(bk[i, j]) * a[j] for j in range(a1 - a0)) for i in range(a1 - a0)]
+            D = [int(c[k][i]) + s for i, s in enumerate(exact_rowdot(b[k], a))]
             x[a0:a1] = decode(D, brow[k], sum(a), a1 - a0, qp)
             Dall.extend(D)
         z_new = soft_threshold(v + x, lam / rho)

@@ -140,3 +140,35 @@ def batch_problem(seed: int = 5, nodes: int = 64, lo: int = 256, hi: int = 65536
     aty = x0 + noise * rng.standard_normal(N)
     return BatchProblem(sizes=sizes, node_key=[k % len(key_bits) for k in range(nodes)], key_bits=tuple(key_bits),
                         x0=x0, aty=aty, lam=lam, rho=rho)
+
+
+def lasso_large_data(seed: int = 3, side: int = 256, frac: float = 0.05, K: int = 16, noise: float = 0.01,
+                     device="cuda"):
+    """The full-scale problem drawn node by node on a torch device (the dense
+    A of N/4 x N doubles is 8.6 GB at N = 65536): x0 as lasso_large (numpy,
+    5% nonzero DCT-domain coefficients, low frequencies favoured), A_k with
+    N(0, 4/N) entries from a seeded torch generator, y = sum_k A_k x0_k +
+    N(0, noise^2).  Returns (x0, node sizes, [A_k], y)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    N = side * side
+    u, v = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
+    w = (1.0 / (1.0 + u + v)).ravel()
+    nnz = int(round(frac * N))
+    pos = rng.choice(N, size=nnz, replace=False, p=w / w.sum())
+    x0 = np.zeros(N)
+    x0[pos] = rng.standard_normal(nnz)
+    sizes = node_sizes(N, K)
+    M = N // 4
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    xd = torch.from_numpy(x0).to(device)
+    A, y, o = [], torch.zeros(M, dtype=torch.float64, device=device), 0
+    for nk in sizes:
+        Ak = torch.randn(M, nk, generator=g, dtype=torch.float64, device=device) * float(np.sqrt(4.0 / N))
+        y += Ak @ xd[o:o + nk]
+        A.append(Ak)
+        o += nk
+    y += noise * torch.randn(M, generator=g, dtype=torch.float64, device=device)
+    return x0, sizes, A, y

@@ -229,3 +229,18 @@ def test_batch_problem_shape():
     bp = W.batch_problem(seed=1, nodes=10, lo=8, hi=100)
     assert len(bp.sizes) == 10 and all(8 <= s <= 100 for s in bp.sizes)
     assert len(bp.aty) == sum(bp.sizes) and bp.node_key[:4] == [0, 1, 2, 0]
+
+
+def test_exact_rowdot_split_equals_python_integers():
+    """The int64 split of exact_rowdot against term-by-term Python integers,
+    including the largest operands the quantizer produces (b = Delta, a = 2 Delta)."""
+    rng = np.random.default_rng(7)
+    delta = 16 << 24
+    b = rng.integers(0, delta + 1, size=(300, 400), dtype=np.int64)
+    b[0, :] = delta
+    a = [int(x) for x in rng.integers(0, 2 * delta + 1, size=400)]
+    a[:5] = [2 * delta] * 5
+    want = [sum(int(b[i, j]) * a[j] for j in range(400)) for i in range(300)]
+    assert O.exact_rowdot(b, a) == want        # split path (b.size > 2^16)
+    small = b[:100, :50]
+    assert O.exact_rowdot(small, a[:50]) == [sum(int(small[i, j]) * a[j] for j in range(50)) for i in range(100)]
