@@ -61,7 +61,7 @@ _hom_sum = _sig("pc2_hom_sum", [_vp, _vp, _vp, _sz, _sz, _vp, _vp])
 _hom_scal = _sig("pc2_hom_scal", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
 
 ST_RANGE, ST_QUANT, ST_TIMEOUT = 1, 2, 4
-OP_ENCRYPT, OP_ENCRYPT_PUBLIC, OP_DECRYPT = 0, 1, 2
+COST_ENCRYPT, COST_ENCRYPT_PUBLIC, COST_DECRYPT = 0, 1, 2  # pc2_key_cost operations
 
 
 class Pc2Error(RuntimeError):
