@@ -78,12 +78,18 @@ int pc2_ctx_set_window(pc2_ctx* ctx, int w);
  * groups still fit in one resident wave: small batches get more lanes per
  * element and finish sooner). */
 int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes);
-/* Autotuner: times every built lane count x window width (4..6) of key-owner
- * encryption (ops bit 0) and/or decryption (bit 1) on `count` elements (at
- * most two resident waves of them) and records the fastest for calls of the
- * same size class (ceil(log2 count)) on this key size in this context.
- * h_result (optional) receives (lanes, window) per tuned op, in that order.
- * Allocates and frees temporary device buffers; synchronises `stream`. */
+/* Runs the two CRT halves of each element's exponentiations in parallel
+ * (one half per two warps of a CTA, recombined after a block barrier) when
+ * the lane count is above one: mode 0 automatic (when the doubled lanes still
+ * fit one resident wave), 1 never, 2 always.  Results do not change. */
+int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
+/* Autotuner: times every built lane count x split (where lanes > 1) x window
+ * width (4..6) of key-owner encryption (ops bit 0) and/or decryption (bit 1)
+ * on `count` elements (at most two resident waves of them) and records the
+ * fastest for calls of the same size class (ceil(log2 count)) on this key
+ * size in this context.  h_result (optional) receives (lanes, window, split)
+ * per tuned op, in that order.  Allocates and frees temporary device
+ * buffers; synchronises `stream`. */
 int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_stream_t stream, int* h_result);
 
 /* ---- keys (host) ------------------------------------------------------ *

@@ -58,10 +58,16 @@ struct pc2_admm {
   int ntiles = 0;
   int mv_T = 1;  // lanes per row of the matvec (fixed at creation: it sets the row tiles)
   DevBuf<double> alpha, Bbar, x, z, v;
-  DevBuf<uint32_t> bq, alpha_hat, zhat, vhat, shat, smont, xhat, D, round_ctr, bitlen;
+  DevBuf<uint32_t> bq, alpha_hat, shat, smont, xhat, D, round_ctr, bitlen;
+  DevBuf<uint32_t> zvhat;  // z-hat (elements [0, N)) then (-v)-hat (from element Npad) in one tiled array
+  uint32_t* zhat = nullptr;
+  uint32_t* vhat = nullptr;
   DevBuf<long long> boff, brow;
   DevBuf<int> node_of, node_off, node_size, tile_node, tile_row0;
-  DevBuf<uint64_t> zq, vq, tmp64;
+  DevBuf<uint64_t> zv, tmp64;  // Gamma2(z) then Gamma2(-v), adjacent (one encryption launch)
+  uint64_t* zq = nullptr;
+  uint64_t* vq = nullptr;
+  int Npad = 0;                 // N rounded up to a whole tile
   DevBuf<unsigned long long> asum;
   std::shared_ptr<void> mvp, modp;  // cached MatvecParams<L2> / ModConst<L2> of n^2
   cudaGraphExec_t graph = nullptr;
@@ -152,11 +158,13 @@ static int dispatch_to_mont(pc2_admm* A, cudaStream_t st) {
 static int round_batched(pc2_admm* A, cudaStream_t st) {
   pc2_ctx* ctx = A->ctx;
   if (cudaMemsetAsync(A->asum.p, 0, A->K * sizeof(unsigned long long), st) != cudaSuccess) return PC2_ECUDA;
-  PC2_TRY(launch_admm_quant(A->z.p, A->v.p, A->N, A->node_of.p, A->zmin, A->scale, A->qmax, A->zq.p, A->vq.p,
+  PC2_TRY(launch_admm_quant(A->z.p, A->v.p, A->N, A->node_of.p, A->zmin, A->scale, A->qmax, A->zq, A->vq,
                             A->asum.p, ctx->status, ctx->sms, st));
-  PC2_TRY(encrypt_round(ctx, A->key, A->zq.p, A->N, A->seed, A->round_ctr.p, 1, 0, A->zhat.p, st));
-  PC2_TRY(encrypt_round(ctx, A->key, A->vq.p, A->N, A->seed, A->round_ctr.p, 2, 0, A->vhat.p, st));
-  PC2_TRY(pc2_hom_add(ctx, A->key, A->zhat.p, A->vhat.p, A->N, A->shat.p, (pc2_stream_t)st));
+  // z-hat and (-v)-hat in one call: elements [0, N) are Gamma2(z) (r-stream kind 1),
+  // [N, 2N) are Gamma2(-v) (kind 2, counter restarting at 0, tiled from element Npad)
+  PC2_TRY(encrypt_round(ctx, A->key, A->zq, 2 * (size_t)A->N, A->seed, A->round_ctr.p, 1, 0, A->zvhat.p, st, 0,
+                        (size_t)A->N, 2, (size_t)A->Npad));
+  PC2_TRY(pc2_hom_add(ctx, A->key, A->zhat, A->vhat, A->N, A->shat.p, (pc2_stream_t)st));
   PC2_TRY(dispatch_to_mont(A, st));
   PC2_TRY(dispatch_matvec(A, 0, A->ntiles, st));
   PC2_TRY(pc2_decrypt(ctx, A->key, A->xhat.p, A->N, A->D.p, (pc2_stream_t)st));
@@ -218,7 +226,7 @@ int pc2_admm_create(pc2_ctx* ctx, const pc2_key* key, const pc2_admm_params* prm
   // node layout and CTA row tiles (a tile never straddles two nodes)
   size_t Ntot = 0;
   for (int k = 0; k < A->K; ++k) Ntot += prm->node_sizes[k] > 0 ? (size_t)prm->node_sizes[k] : 0;
-  A->mv_T = pick_config(ctx, OP_MATVEC, A->L2, Ntot).first;
+  A->mv_T = pick_config(ctx, OP_MATVEC, A->L2, Ntot).T;
   const int G = kThreads / A->mv_T;
   A->off.assign(A->K + 1, 0);
   A->boffh.assign(A->K, 0);
@@ -239,19 +247,24 @@ int pc2_admm_create(pc2_ctx* ctx, const pc2_key* key, const pc2_admm_params* prm
   }
   A->tile_start.push_back((int)tnode.size());
   A->N = A->off[A->K];
+  A->Npad = (A->N + 31) / 32 * 32;
   A->ntiles = (int)tnode.size();
   const int N = A->N;
   std::vector<int> nsz(A->K);
   for (int k = 0; k < A->K; ++k) nsz[k] = prm->node_sizes[k];
   const size_t ctw = A->ctw();
   if (A->alpha.alloc(N) || A->Bbar.alloc(bsum) || A->x.alloc(N) || A->z.alloc(N) || A->v.alloc(N) ||
-      A->bq.alloc(bsum) || A->alpha_hat.alloc(ctw) || A->zhat.alloc(ctw) || A->vhat.alloc(ctw) ||
+      A->bq.alloc(bsum) || A->alpha_hat.alloc(ctw) || A->zvhat.alloc(2 * pc2_tiled_words(A->Npad, A->L2)) ||
       A->shat.alloc(ctw) || A->smont.alloc((size_t)N * A->L2) || A->xhat.alloc(ctw) ||
       A->D.alloc(pc2_tiled_words(N, A->Lh)) || A->round_ctr.alloc(1) || A->bitlen.alloc(1) || A->boff.alloc(A->K) ||
       A->brow.alloc(N) || A->node_of.alloc(N) || A->node_off.alloc(A->K + 1) || A->node_size.alloc(A->K) ||
-      A->tile_node.alloc(A->ntiles) || A->tile_row0.alloc(A->ntiles) || A->zq.alloc(N) || A->vq.alloc(N) ||
+      A->tile_node.alloc(A->ntiles) || A->tile_row0.alloc(A->ntiles) || A->zv.alloc(2 * (size_t)N) ||
       A->tmp64.alloc(bsum > N ? bsum : N) || A->asum.alloc(A->K))
     return PC2_ENOMEM;
+  A->zq = A->zv.p;
+  A->vq = A->zv.p + N;
+  A->zhat = A->zvhat.p;
+  A->vhat = A->zvhat.p + pc2_tiled_words(A->Npad, A->L2);
   auto h2d = [&](void* d, const void* h, size_t bytes) {
     return cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
   };
@@ -319,13 +332,13 @@ int pc2_admm_round(pc2_admm* A, int rounds, pc2_stream_t stream) {
     if (A->per_node) {
       // every node launched on its own (the plain per-node path)
       if (cudaMemsetAsync(A->asum.p, 0, A->K * sizeof(unsigned long long), st) != cudaSuccess) return PC2_ECUDA;
-      PC2_TRY(launch_admm_quant(A->z.p, A->v.p, A->N, A->node_of.p, A->zmin, A->scale, A->qmax, A->zq.p, A->vq.p,
+      PC2_TRY(launch_admm_quant(A->z.p, A->v.p, A->N, A->node_of.p, A->zmin, A->scale, A->qmax, A->zq, A->vq,
                                 A->asum.p, ctx->status, ctx->sms, st));
       for (int k = 0; k < A->K; ++k) {
         const int o = A->off[k], nk = A->off[k + 1] - o;
-        PC2_TRY(encrypt_round(ctx, A->key, A->zq.p + o, nk, A->seed, A->round_ctr.p, 1, o, A->zhat.p, st, o));
-        PC2_TRY(encrypt_round(ctx, A->key, A->vq.p + o, nk, A->seed, A->round_ctr.p, 2, o, A->vhat.p, st, o));
-        PC2_TRY(hom_add_at(ctx, A->key, A->zhat.p, A->vhat.p, nk, A->shat.p, st, o));
+        PC2_TRY(encrypt_round(ctx, A->key, A->zq + o, nk, A->seed, A->round_ctr.p, 1, o, A->zhat, st, o));
+        PC2_TRY(encrypt_round(ctx, A->key, A->vq + o, nk, A->seed, A->round_ctr.p, 2, o, A->vhat, st, o));
+        PC2_TRY(hom_add_at(ctx, A->key, A->zhat, A->vhat, nk, A->shat.p, st, o));
       }
       PC2_TRY(dispatch_to_mont(A, st));
       for (int k = 0; k < A->K; ++k)
@@ -403,8 +416,8 @@ int pc2_admm_set(pc2_admm* A, const double* d_x, const double* d_z, const double
 int pc2_admm_buffers(pc2_admm* A, const uint32_t** zhat, const uint32_t** vhat, const uint32_t** xhat,
                      const uint32_t** alpha_hat, const uint32_t** D, int* N) {
   if (!A) return PC2_EINVAL;
-  if (zhat) *zhat = A->zhat.p;
-  if (vhat) *vhat = A->vhat.p;
+  if (zhat) *zhat = A->zhat;
+  if (vhat) *vhat = A->vhat;
   if (xhat) *xhat = A->xhat.p;
   if (alpha_hat) *alpha_hat = A->alpha_hat.p;
   if (D) *D = A->D.p;

@@ -94,24 +94,40 @@ static int log2_bucket(size_t count) {
   return b;
 }
 
-std::pair<int, int> pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
+LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
   int n = 0;
   const int* set = lane_set(op, limbs, &n);
+  const bool can_split = op != OP_MATVEC;
+  const double cap = (double)ctx->sms * 384.0;  // resident threads of one wave (about 384 per SM)
+  auto auto_split = [&](int T) {
+    if (!can_split || T < 2 || ctx->split == 1) return false;
+    return ctx->split == 2 || (double)count * 2 * T <= cap;
+  };
   if (ctx->lanes)
     for (int i = 0; i < n; ++i)
-      if (set[i] == ctx->lanes) return {ctx->lanes, 0};
+      if (set[i] == ctx->lanes) return LaneCfg{ctx->lanes, 0, auto_split(ctx->lanes)};
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto it = ctx->tuned.find(std::make_tuple(op, limbs, log2_bucket(count)));
-    if (it != ctx->tuned.end()) return it->second;
+    if (it != ctx->tuned.end())
+      return LaneCfg{std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second) != 0};
   }
-  // the largest lane count whose groups still fit in one resident wave
-  // (about 384 threads per SM for these kernels)
-  const double cap = (double)ctx->sms * 384.0;
-  int T = set[0];
-  for (int i = 0; i < n; ++i)
-    if ((double)count * set[i] <= cap) T = set[i];
-  return {T, 0};
+  // the most lanes per element that still fit one wave; split at equal lanes
+  LaneCfg best{set[0], 0, false};
+  int best_lanes = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int s = 0; s < 2; ++s) {
+      if (s && (!can_split || set[i] < 2 || ctx->split == 1)) continue;
+      if (!s && ctx->split == 2 && set[i] > 1 && can_split) continue;
+      const int le = set[i] * (s ? 2 : 1);
+      if ((double)count * le > cap) continue;
+      if (le > best_lanes || (le == best_lanes && s)) {
+        best = LaneCfg{set[i], 0, s != 0};
+        best_lanes = le;
+      }
+    }
+  }
+  return best;
 }
 
 template <int Lh, int T>
@@ -133,8 +149,8 @@ static int with_crt_lanes(int T, Fn fn) {
 template <int Lh>
 static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
                    uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
-  const auto cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
-  const int w = cfg.second ? cfg.second : ctx->window;
+  const LaneCfg cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
+  const int w = cfg.w ? cfg.w : ctx->window;
   int rc;
   auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w,
                                      [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, w, P); }, &rc);
@@ -145,18 +161,21 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->stream = stream;
   P->e0 = e0;
   P->mwords = mw ? Lh : 2;
-  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
-    return launch_enc_crt<Lh, decltype(tt)::value>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms,
-                                                   st, 0);
+  return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
+    constexpr int T = decltype(tt)::value;
+    if constexpr (T > 1)
+      if (cfg.split)
+        return launch_enc_crt2<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
+    return launch_enc_crt<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
   });
 }
 
 template <int Lh>
 static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, size_t count, uint64_t seed,
                          const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* out, cudaStream_t st,
-                         size_t base) {
-  const auto cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
-  const int w = cfg.second ? cfg.second : ctx->window;
+                         size_t base, size_t split, uint32_t kind2, size_t base2) {
+  const LaneCfg cfg = pick_config(ctx, OP_ENC_CRT, Lh, count);
+  const int w = cfg.w ? cfg.w : ctx->window;
   int rc;
   auto P0 = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w,
                                      [&](EncCrtParams<Lh>& P) { return make_enc_crt<Lh>(*key, w, P); }, &rc);
@@ -168,25 +187,42 @@ static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, 
   P->mwords = 2;
   P->round_ptr = round_ptr;
   P->kind = kind;
-  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
-    return launch_enc_crt<Lh, decltype(tt)::value>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status,
-                                                   ctx->sms, st, base);
+  P->split = split;
+  P->kind2 = kind2;
+  P->base2 = base2;
+  return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
+    constexpr int T = decltype(tt)::value;
+    if constexpr (T > 1)
+      if (cfg.split)  // both vectors in one launch
+        return launch_enc_crt2<Lh, T>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st,
+                                      base);
+    if (split >= count)
+      return launch_enc_crt<Lh, T>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
+    // the one-vector kernel: the two vectors one after the other
+    int r = launch_enc_crt<Lh, T>(*P, m64, nullptr, split, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
+    if (r != PC2_OK) return r;
+    P->kind = kind2;
+    return launch_enc_crt<Lh, T>(*P, m64 + split, nullptr, count - split, out, ctx_scratch, ctx, ctx->status,
+                                 ctx->sms, st, base2);
   });
 }
 
 int encrypt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t count, uint64_t seed,
                   const uint32_t* round_ptr, uint32_t kind, uint64_t e0, uint32_t* d_ct, cudaStream_t st,
-                  size_t base) {
+                  size_t base, size_t split, uint32_t kind2, size_t base2) {
   if (!ctx || !key || !key->priv) return PC2_EKEY;
   if (!count) return PC2_OK;
+#define PC2_CALL_ROUND(L) \
+  enc_crt_round<L>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base, split, kind2, base2)
   switch (key->Lh) {
-    case 8: return enc_crt_round<8>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
-    case 16: return enc_crt_round<16>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
-    case 32: return enc_crt_round<32>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
-    case 64: return enc_crt_round<64>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
-    case 96: return enc_crt_round<96>(ctx, key, d_m, count, seed, round_ptr, kind, e0, d_ct, st, base);
+    case 8: return PC2_CALL_ROUND(8);
+    case 16: return PC2_CALL_ROUND(16);
+    case 32: return PC2_CALL_ROUND(32);
+    case 64: return PC2_CALL_ROUND(64);
+    case 96: return PC2_CALL_ROUND(96);
     default: return PC2_EUNSUPPORTED;
   }
+#undef PC2_CALL_ROUND
 }
 
 template <int L2>
@@ -208,13 +244,16 @@ static int enc_pub(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
 template <int Lh>
 static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
                size_t base = 0) {
-  const auto cfg = pick_config(ctx, OP_DEC, Lh, count);
-  const int w = cfg.second ? cfg.second : ctx->window;
+  const LaneCfg cfg = pick_config(ctx, OP_DEC, Lh, count);
+  const int w = cfg.w ? cfg.w : ctx->window;
   int rc;
   auto P = cached<DecParams<Lh>>(key, KIND_DEC, w, [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, w, p); }, &rc);
   if (!P) return rc;
-  return with_crt_lanes<Lh>(cfg.first, [&](auto tt) {
-    return launch_dec_crt<Lh, decltype(tt)::value>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
+  return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
+    constexpr int T = decltype(tt)::value;
+    if constexpr (T > 1)
+      if (cfg.split) return launch_dec_crt2<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
+    return launch_dec_crt<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
   });
 }
 
@@ -385,6 +424,12 @@ int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes) {
   return PC2_OK;
 }
 
+int pc2_ctx_set_split(pc2_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) return PC2_EINVAL;
+  ctx->split = mode;
+  return PC2_OK;
+}
+
 int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_stream_t stream, int* h_result) {
   if (!ctx || !key || !count || (ops & ~3) || !ops) return PC2_EINVAL;
   if (!key->priv) return PC2_EKEY;
@@ -407,31 +452,39 @@ int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_st
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int saved_lanes = ctx->lanes, saved_window = ctx->window;
+  const int saved_lanes = ctx->lanes, saved_window = ctx->window, saved_split = ctx->split;
   int rc = PC2_OK, res_i = 0;
   for (int op : {OP_ENC_CRT, OP_DEC}) {
     if (!((op == OP_ENC_CRT && (ops & 1)) || (op == OP_DEC && (ops & 2)))) continue;
     int nl = 0;
     const int* set = lane_set(op, Lh, &nl);
+    // decryption times the ciphertexts of an encryption pass
+    if (op == OP_DEC) {
+      ctx->lanes = 0;
+      ctx->window = saved_window;
+      ctx->split = saved_split;
+      rc = pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream);
+      if (rc != PC2_OK) break;
+    }
     float best = 1e30f;
-    std::pair<int, int> pick{set[0], 0};
+    std::tuple<int, int, int> pick{set[0], 0, 0};
     for (int i = 0; i < nl && rc == PC2_OK; ++i) {
-      for (int w = 4; w <= kMaxWin && rc == PC2_OK; ++w) {
-        ctx->lanes = set[i];
-        ctx->window = w;
-        // decryption times the ciphertexts of the encryption pass (made once below when only ops == 2)
-        if (op == OP_DEC && !(ops & 1) && i == 0 && w == 4) rc = pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream);
-        if (rc != PC2_OK) break;
-        cudaEventRecord(e0, st);
-        rc = op == OP_ENC_CRT ? pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream)
-                              : pc2_decrypt(ctx, key, dct, n, dout, stream);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = PC2_ECUDA;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == PC2_OK && ms < best) {
-          best = ms;
-          pick = {set[i], w};
+      for (int s = 0; s < (set[i] > 1 ? 2 : 1) && rc == PC2_OK; ++s) {
+        for (int w = 4; w <= kMaxWin && rc == PC2_OK; ++w) {
+          ctx->lanes = set[i];
+          ctx->split = s ? 2 : 1;
+          ctx->window = w;
+          cudaEventRecord(e0, st);
+          rc = op == OP_ENC_CRT ? pc2_encrypt(ctx, key, dm, n, 1, 1, 0, dct, stream)
+                                : pc2_decrypt(ctx, key, dct, n, dout, stream);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) rc = PC2_ECUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rc == PC2_OK && ms < best) {
+            best = ms;
+            pick = std::make_tuple(set[i], w, s);
+          }
         }
       }
     }
@@ -441,12 +494,14 @@ int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_st
       ctx->tuned[std::make_tuple(op, Lh, log2_bucket(count))] = pick;
     }
     if (h_result) {
-      h_result[res_i++] = pick.first;
-      h_result[res_i++] = pick.second;
+      h_result[res_i++] = std::get<0>(pick);
+      h_result[res_i++] = std::get<1>(pick);
+      h_result[res_i++] = std::get<2>(pick);
     }
   }
   ctx->lanes = saved_lanes;
   ctx->window = saved_window;
+  ctx->split = saved_split;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);

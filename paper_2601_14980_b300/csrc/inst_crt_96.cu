@@ -10,4 +10,11 @@ template int launch_enc_crt<96, 8>(const EncCrtParams<96>&, const uint64_t*, con
 template int launch_dec_crt<96, 8>(const DecParams<96>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
 template int launch_dec_crt_fixed<96, 2>(const DecParams<96>&, const uint32_t*, size_t, uint32_t*, uint32_t*, size_t, int, cudaStream_t);
 
+template int launch_enc_crt2<96, 2>(const EncCrtParams<96>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
+template int launch_dec_crt2<96, 2>(const DecParams<96>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
+template int launch_enc_crt2<96, 4>(const EncCrtParams<96>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
+template int launch_dec_crt2<96, 4>(const DecParams<96>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
+template int launch_enc_crt2<96, 8>(const EncCrtParams<96>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
+template int launch_dec_crt2<96, 8>(const DecParams<96>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
+
 }  // namespace pc2

@@ -208,6 +208,7 @@ int make_enc_crt(const pc2_key& k, int w, EncCrtParams<Lh>& P) {
   const Big pinv2 = mulmod(pinv, pinv, q2);
   const Mont Mq(q2, Lh);
   mulmod(pinv2, Mq.R1, q2).to_words(P.pinv2R, Lh);
+  P.split = ~0ull;
   return PC2_OK;
 }
 

@@ -286,6 +286,119 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
   }
 }
 
+// ------------------------------------------------------------------ split CRT halves
+// The results of k_enc_crt / k_dec_crt with the two CRT halves of an element
+// computed at the same time: in a CTA the first half of the lane groups (two
+// warps) works mod p^2 and the second half mod q^2 on the same elements, and
+// the recombination follows a block barrier.  Each warp runs one exponent's
+// schedule, so control flow stays uniform.  Halves the time per element when
+// the batch leaves most of the GPU idle (small batches; T > 1).
+// Encryption also takes a second vector in the same launch: elements
+// e >= P.split use r-stream kind2, counter e0 + (e - split) and tiled output
+// position base2 + (e - split).
+template <int Lh, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const __grid_constant__ EncCrtParams<Lh> P,
+                                                      const uint64_t* __restrict__ m64,
+                                                      const uint32_t* __restrict__ mwide, size_t count,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
+                                                      int tabw, int* status, size_t base_out) {
+  static_assert(T > 1, "one CRT half per two warps needs lane groups");
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const int H = ly.G / 2;  // elements per CTA and pass
+  const int half = ly.gl >= H ? 1 : 0;
+  const int pe = ly.gl - half * H;
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  const int SW = 2 * Lh + 4;
+  const Col X = ly.slot(scratch, tabw + 0 * SW), GM = ly.slot(scratch, tabw + 1 * SW),
+            A = ly.slot(scratch, tabw + 2 * SW), B = ly.slot(scratch, tabw + 3 * SW),
+            C = ly.slot(scratch, tabw + 4 * SW), TT = ly.slot(scratch, tabw + 5 * SW),
+            CH = ly.slot(scratch, tabw + 6 * SW);
+  const ModConst<Lh>& M = half ? P.mq : P.mp;
+  const Sched<kMaxSched>& E = half ? P.eq : P.ep;
+  for (size_t base = (size_t)blockIdx.x * H; base < count; base += (size_t)gridDim.x * H) {
+    size_t e = base + pe;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    const bool second = e >= P.split;
+    const size_t ei = second ? e - P.split : e;
+    const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | (second ? P.kind2 : P.kind)) : P.stream;
+    gen_r(X, P.seed, sid, P.e0 + ei, Lh + 2, 2 * Lh);
+    make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid && half == 0, status);
+    enc_half<Lh, T>(M, E, X, GM, CH, A, B, C, TT, tab, bsh, g);
+    __syncthreads();
+    if (half == 0) {
+      // Eq. (gA-C-B) with c_q from the partner group (gl + H) of this CTA
+      const Col CP = CH, CQ{CH.p + H, CH.s};
+      if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
+      g_copy_param(B, P.pinv2R, Lh);
+      g_mont(C, A, B, P.mq.n, P.mq.np, Lh, TT);
+      g_mul(X, C, Lh, PArr{P.p2}, Lh);
+      uint64_t c = 0;
+      for (int j = 0; j < 2 * Lh; ++j) {
+        c += (uint64_t)X[j] + (j < Lh ? CP[j] : 0u);
+        X[j] = (uint32_t)c;
+        c >>= 32;
+      }
+      if (valid) write_tiled<T>(out, (second ? P.base2 : base_out) + ei, X, 2 * Lh, g);
+    }
+    __syncthreads();
+  }
+}
+
+template <int Lh, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt2(const __grid_constant__ DecParams<Lh> P,
+                                                      const uint32_t* __restrict__ ct, size_t count,
+                                                      uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
+                                                      int tabw, size_t ebase) {
+  static_assert(T > 1, "one CRT half per two warps needs lane groups");
+  constexpr int Lp = Lh / 2;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const int H = ly.G / 2;
+  const int half = ly.gl >= H ? 1 : 0;
+  const int pe = ly.gl - half * H;
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  const int SW = 2 * Lh + 4;
+  const Col X = ly.slot(scratch, tabw + 0 * SW), A = ly.slot(scratch, tabw + 1 * SW),
+            B = ly.slot(scratch, tabw + 2 * SW), C = ly.slot(scratch, tabw + 3 * SW),
+            TT = ly.slot(scratch, tabw + 4 * SW), MH = ly.slot(scratch, tabw + 5 * SW);
+  const ModConst<Lh>& M = half ? P.mq : P.mp;
+  const Sched<kMaxSchedHalf>& E = half ? P.eq : P.ep;
+  const uint32_t* h = half ? P.q : P.p;
+  const uint32_t hnp = half ? P.qnp : P.pnp;
+  const uint32_t* hinvlo = half ? P.qinvlo : P.pinvlo;
+  const uint32_t* hhR = half ? P.hqR : P.hpR;
+  for (size_t base = (size_t)blockIdx.x * H; base < count; base += (size_t)gridDim.x * H) {
+    size_t e = base + pe;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(ebase + e, j, 2 * Lh)];
+    dec_half<Lh, T>(M, E, h, hnp, hinvlo, hhR, X, MH, A, B, C, TT, tab, bsh, g);
+    __syncthreads();
+    if (half == 0) {
+      // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q], m_q from the partner group
+      const Col MP = MH, MQ{MH.p + H, MH.s};
+      if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{P.q}, Lp);
+      g_copy_param(B, P.pinvqR, Lp);
+      g_mont(C, A, B, P.q, P.qnp, Lp, TT);
+      g_mul(X, C, Lp, PArr{P.p}, Lp);
+      uint64_t c = 0;
+      for (int j = 0; j < Lh; ++j) {
+        c += (uint64_t)X[j] + (j < Lp ? MP[j] : 0u);
+        X[j] = (uint32_t)c;
+        c >>= 32;
+      }
+      if (valid) write_tiled<T>(out, ebase + e, X, Lh, g);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ homomorphic ops
 template <int L2, int T>
 __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_sum(const __grid_constant__ HomParams<L2> P, size_t count,

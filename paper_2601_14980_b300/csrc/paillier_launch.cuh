@@ -104,4 +104,37 @@ int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* 
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
+// Split-halves variants (T > 1): same arguments, same results.
+template <int Lh, int T>
+int launch_enc_crt2(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                   ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base) {
+  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
+  auto kern = k_enc_crt2<Lh, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  const int tabw = (1 << (w - 1)) * Lh;
+  const size_t per_group = (size_t)tabw + 8 * (size_t)(2 * Lh + 4);
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, m64, mwide, count, out, scratch, tabw, status, base);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+template <int Lh, int T>
+int launch_dec_crt2(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
+                   void* sctx, int sms, cudaStream_t st, size_t base) {
+  const size_t smem = (size_t)Lh * (kThreads / T) * 4;
+  auto kern = k_dec_crt2<Lh, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const int w = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  const int tabw = (1 << (w - 1)) * Lh;
+  const size_t per_group = (size_t)tabw + 7 * (size_t)(2 * Lh + 4);
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, ct, count, out, scratch, tabw, base);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
 }  // namespace pc2

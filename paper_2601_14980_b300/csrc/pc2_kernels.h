@@ -24,6 +24,14 @@ int launch_enc_pub(const EncPubParams<L2>& P, const uint64_t* m64, const uint32_
 template <int Lh, int T>
 int launch_dec_crt(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
                    void* sctx, int sms, cudaStream_t st, size_t base = 0);
+// The same operations with the two CRT halves of each element computed in
+// parallel (T > 1): lower latency for batches that leave the GPU idle.
+template <int Lh, int T>
+int launch_enc_crt2(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,
+                    ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base = 0);
+template <int Lh, int T>
+int launch_dec_crt2(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, ScratchFn scratch_fn,
+                    void* sctx, int sms, cudaStream_t st, size_t base = 0);
 template <int Lh, int T>
 int launch_dec_crt_fixed(const DecParams<Lh>& P, const uint32_t* ct, size_t count, uint32_t* out, uint32_t* scratch,
                          size_t scratch_words, int sms, cudaStream_t st);

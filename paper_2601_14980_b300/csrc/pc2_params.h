@@ -68,7 +68,9 @@ struct EncCrtParams {
   int32_t mwords;
   const uint32_t* round_ptr;
   uint32_t kind;
-  uint32_t pad_;
+  uint32_t kind2;  // elements e >= split form a second vector (split-halves kernel only):
+  uint64_t split;  // r-stream kind2, counter e0 + (e - split), tiled output position base2 + (e - split)
+  uint64_t base2;
 };
 
 // CRT decryption (Lh = limbs of n; p, q have Lh/2 limbs).

@@ -414,17 +414,25 @@ def set_lanes(ctx: Context, lanes: int):
 
 
 def autotune(ctx: Context, key: Key, count: int, encrypt: bool = True, decrypt: bool = True, stream=None) -> dict:
-    """Run the library's autotuner for `count`-element calls; returns the chosen (lanes, window) per op."""
+    """Run the library's autotuner for `count`-element calls; returns the chosen (lanes, window, split) per op."""
     ops = (1 if encrypt else 0) | (2 if decrypt else 0)
-    res = (_i * 4)()
+    res = (_i * 6)()
     _check(_autotune(ctx.h, key.h, count, ops, _stream(stream), res), "pc2_autotune")
     out, i = {}, 0
     if encrypt:
-        out["encrypt"] = (res[0], res[1])
-        i = 2
+        out["encrypt"] = (res[0], res[1], res[2])
+        i = 3
     if decrypt:
-        out["decrypt"] = (res[i], res[i + 1])
+        out["decrypt"] = (res[i], res[i + 1], res[i + 2])
     return out
+
+
+_ctx_set_split = _sig("pc2_ctx_set_split", [_vp, _i])
+
+
+def set_split(ctx: Context, mode: int):
+    """CRT halves in parallel: 0 automatic, 1 never, 2 whenever lanes > 1."""
+    _check(_ctx_set_split(ctx.h, mode), "pc2_ctx_set_split")
 
 
 class _BatchParams(ctypes.Structure):

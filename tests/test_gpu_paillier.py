@@ -152,21 +152,24 @@ def test_lanes_and_windows_bit_identical(env, nbits):
     ref = _oracle_ct(ko, m[:4])
     L2 = 2 * kg.limbs
     try:
-        for lanes in (1, 2, 4, 8):
-            for w in (0, 4, 6):
-                pc2.set_lanes(ctx, lanes)
-                ctx.set_window(w)
-                try:
-                    ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM)
-                except pc2.Pc2Error as e:
-                    assert e.code == -8 and (lanes == 8 and kg.limbs == 8)  # not built for this size
-                    continue
-                got = pc2.tiled_to_ints(ctx, ct, count, L2)
-                assert got[:4] == ref, (lanes, w)
-                dec = pc2.tiled_to_ints(ctx, pc2.decrypt(ctx, kg, ct, count), count, kg.limbs)
-                assert dec == [int(x) for x in m], (lanes, w)
+        for lanes, w, split in [(l, w, s) for l in (1, 2, 4, 8) for w in (0, 4, 6) for s in (1, 2)]:
+            if lanes == 1 and split == 2:
+                continue
+            pc2.set_lanes(ctx, lanes)
+            pc2.set_split(ctx, split)      # 1: halves one after the other, 2: in parallel
+            ctx.set_window(w)
+            try:
+                ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM)
+            except pc2.Pc2Error as e:
+                assert e.code == -8 and (lanes == 8 and kg.limbs == 8)  # not built for this size
+                continue
+            got = pc2.tiled_to_ints(ctx, ct, count, L2)
+            assert got[:4] == ref, (lanes, w, split)
+            dec = pc2.tiled_to_ints(ctx, pc2.decrypt(ctx, kg, ct, count), count, kg.limbs)
+            assert dec == [int(x) for x in m], (lanes, w, split)
     finally:
         pc2.set_lanes(ctx, 0)
+        pc2.set_split(ctx, 0)
         ctx.set_window(0)
 
 
@@ -174,8 +177,8 @@ def test_autotune_records_and_stays_exact(env):
     torch, pc2, ctx = env
     kg, ko = _keys(pc2, 1024, seed=7)
     res = pc2.autotune(ctx, kg, 300)
-    assert res["encrypt"][0] in (1, 2, 4, 8) and 4 <= res["encrypt"][1] <= 6
-    assert res["decrypt"][0] in (1, 2, 4, 8) and 4 <= res["decrypt"][1] <= 6
+    assert res["encrypt"][0] in (1, 2, 4, 8) and 4 <= res["encrypt"][1] <= 6 and res["encrypt"][2] in (0, 1)
+    assert res["decrypt"][0] in (1, 2, 4, 8) and 4 <= res["decrypt"][1] <= 6 and res["decrypt"][2] in (0, 1)
     m = W.plaintexts_u64(300, seed=8)
     ct = pc2.encrypt(ctx, kg, torch.from_numpy(m.view(np.int64)).cuda(), SEED, STREAM)
     assert pc2.tiled_to_ints(ctx, ct, 3, 2 * kg.limbs) == _oracle_ct(ko, m[:3])
