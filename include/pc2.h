@@ -212,6 +212,12 @@ int pc2_admm_set(pc2_admm* admm, const double* d_x, const double* d_z, const dou
 /* Device pointers of the last round's ciphertexts (tiled) and decrypted integers, and N. */
 int pc2_admm_buffers(pc2_admm* admm, const uint32_t** zhat, const uint32_t** vhat, const uint32_t** xhat,
                      const uint32_t** alpha_hat, const uint32_t** D, int* N);
+/* Form of the encrypted matvec: 0 automatic (windows spread over CTAs when
+ * the row tiles alone would fill less than half of the GPU), 1 one CTA per
+ * row tile, 2 every (row tile, bucket window) pair its own work item, then a
+ * per-row combination.  Results do not change; the captured round graph is
+ * rebuilt on the next round. */
+int pc2_admm_set_matvec(pc2_admm* admm, int mode);
 /* Bucket window c, windows per exponent, CTA row tiles of the matvec. */
 int pc2_admm_info(const pc2_admm* admm, int* c, int* nwin, int* ntiles);
 

@@ -12,6 +12,7 @@
 // counter); the per-node path launches each node separately.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -57,6 +58,8 @@ struct pc2_admm {
   std::vector<long long> boffh;
   int ntiles = 0;
   int mv_T = 1;  // lanes per row of the matvec (fixed at creation: it sets the row tiles)
+  int mv_mode = 0;  // matvec form: 0 automatic, 1 rows per CTA, 2 windows spread over CTAs
+  DevBuf<uint32_t> part;  // window-parallel partial products (nwin x N, tiled)
   DevBuf<double> alpha, Bbar, x, z, v;
   DevBuf<uint32_t> bq, alpha_hat, shat, smont, xhat, D, round_ctr, bitlen;
   DevBuf<uint32_t> zvhat;  // z-hat (elements [0, N)) then (-v)-hat (from element Npad) in one tiled array
@@ -94,6 +97,19 @@ static int matvec_launch_t(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
   }
   MatvecParams<L2> P = *std::static_pointer_cast<MatvecParams<L2>>(A->mvp);
   P.ntiles = ntl;
+  // few row tiles: spread the bucket windows of each row over CTAs too
+  const int cap = matvec_win_grid<L2, T>(1 << 30, A->ctx->sms);
+  if (cap < 1) return PC2_ECUDA;
+  const bool win_par = A->nwin > 1 && (A->mv_mode == 2 || (A->mv_mode == 0 && 2 * ntl < cap));
+  if (win_par) {
+    const int grid = std::min(ntl * A->nwin, cap);
+    uint32_t* scr = ctx_scratch_get(A->ctx, matvec_scratch_words<L2, T>(A->c, grid) * 4);
+    if (!scr) return PC2_ENOMEM;
+    if (!A->part.p && A->part.alloc(pc2_tiled_words((size_t)A->N * A->nwin, L2))) return PC2_ENOMEM;
+    return launch_matvec_win<L2, T>(P, A->alpha_hat.p, A->smont.p, A->bq.p, A->boff.p, A->node_off.p,
+                                    A->tile_node.p + tile0, A->tile_row0.p + tile0, A->N, A->part.p, A->xhat.p, scr,
+                                    grid, A->ctx->sms, st);
+  }
   const int grid = matvec_grid<L2, T>(ntl, A->ctx->sms);
   if (grid < 1) return PC2_ECUDA;
   uint32_t* scr = ctx_scratch_get(A->ctx, matvec_scratch_words<L2, T>(A->c, grid) * 4);
@@ -422,6 +438,16 @@ int pc2_admm_buffers(pc2_admm* A, const uint32_t** zhat, const uint32_t** vhat, 
   if (alpha_hat) *alpha_hat = A->alpha_hat.p;
   if (D) *D = A->D.p;
   if (N) *N = A->N;
+  return PC2_OK;
+}
+
+int pc2_admm_set_matvec(pc2_admm* A, int mode) {
+  if (!A || mode < 0 || mode > 2) return PC2_EINVAL;
+  if (A->graph) {
+    cudaGraphExecDestroy(A->graph);
+    A->graph = nullptr;
+  }
+  A->mv_mode = mode;
   return PC2_OK;
 }
 

@@ -16,4 +16,13 @@ template int launch_matvec<128, 8>(const MatvecParams<128>&, const uint32_t*, co
                                    cudaStream_t);
 template int matvec_grid<128, 8>(int, int);
 
+template int launch_matvec_win<128, 4>(const MatvecParams<128>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<128, 4>(int, int);
+template int launch_matvec_win<128, 8>(const MatvecParams<128>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<128, 8>(int, int);
+
 }  // namespace pc2

@@ -22,4 +22,17 @@ template int launch_matvec<16, 4>(const MatvecParams<16>&, const uint32_t*, cons
                                    cudaStream_t);
 template int matvec_grid<16, 4>(int, int);
 
+template int launch_matvec_win<16, 1>(const MatvecParams<16>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<16, 1>(int, int);
+template int launch_matvec_win<16, 2>(const MatvecParams<16>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<16, 2>(int, int);
+template int launch_matvec_win<16, 4>(const MatvecParams<16>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<16, 4>(int, int);
+
 }  // namespace pc2

@@ -28,4 +28,21 @@ template int launch_matvec<64, 8>(const MatvecParams<64>&, const uint32_t*, cons
                                    cudaStream_t);
 template int matvec_grid<64, 8>(int, int);
 
+template int launch_matvec_win<64, 1>(const MatvecParams<64>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<64, 1>(int, int);
+template int launch_matvec_win<64, 2>(const MatvecParams<64>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<64, 2>(int, int);
+template int launch_matvec_win<64, 4>(const MatvecParams<64>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<64, 4>(int, int);
+template int launch_matvec_win<64, 8>(const MatvecParams<64>&, const uint32_t*, const uint32_t*, const uint32_t*,
+                                      const long long*, const int*, const int*, const int*, int, uint32_t*, uint32_t*,
+                                      uint32_t*, int, int, cudaStream_t);
+template int matvec_win_grid<64, 8>(int, int);
+
 }  // namespace pc2

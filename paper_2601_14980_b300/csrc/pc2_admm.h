@@ -35,5 +35,14 @@ int launch_matvec(const MatvecParams<L2>& P, const uint32_t* alpha_hat, const ui
                   uint32_t* out, uint32_t* scratch, int grid, cudaStream_t st);
 template <int L2, int T>
 int matvec_grid(int ntiles, int sms);
+// Window-parallel form of the same product (few row tiles): part holds
+// nwin x N partial products (tiled, L2 limbs).
+template <int L2, int T>
+int launch_matvec_win(const MatvecParams<L2>& P, const uint32_t* alpha_hat, const uint32_t* smont, const uint32_t* bq,
+                      const long long* boff, const int* node_off, const int* tile_node, const int* tile_row0, int N,
+                      uint32_t* part, uint32_t* out, uint32_t* scratch, int grid, int sms, cudaStream_t st);
+template <int L2, int T>
+int matvec_win_grid(int items, int sms);
+
 
 }  // namespace pc2

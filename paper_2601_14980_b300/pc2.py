@@ -298,6 +298,7 @@ _admm_round_plain = _sig("pc2_admm_round_plain", [_vp, _i, _vp])
 _admm_get = _sig("pc2_admm_get", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32), _vp])
 _admm_set = _sig("pc2_admm_set", [_vp, _vp, _vp, _vp, _u32, _vp])
 _admm_buffers = _sig("pc2_admm_buffers", [_vp] + [ctypes.POINTER(_vp)] * 5 + [ctypes.POINTER(_i)])
+_admm_set_matvec = _sig("pc2_admm_set_matvec", [_vp, _i])
 _admm_info = _sig("pc2_admm_info", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)])
 
 
@@ -363,6 +364,10 @@ class Admm:
         n = _i()
         _check(_admm_buffers(self.h, *[ctypes.byref(p) for p in ps], ctypes.byref(n)), "pc2_admm_buffers")
         return dict(zip(["zhat", "vhat", "xhat", "alpha_hat", "D"], [p.value for p in ps]), N=n.value)
+
+    def set_matvec(self, mode: int):
+        """0 automatic, 1 one CTA per row tile, 2 bucket windows spread over CTAs."""
+        _check(_admm_set_matvec(self.h, mode), "pc2_admm_set_matvec")
 
     def info(self) -> dict:
         c, nw, nt = _i(), _i(), _i()

@@ -162,3 +162,23 @@ def test_lanes_per_element_rounds_bit_exact(env, nbits, lanes):
     finally:
         pc2.set_lanes(ctx, 0)
     assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("nbits", [512, 2048])
+def test_matvec_forms_bit_identical(env, nbits):
+    """Rows per CTA and windows spread over CTAs give the same iterates (and the oracle's)."""
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=6, M=40, N=90, nnz=5, K=3)      # nodes of 30: ragged row tiles
+    ref = None
+    for mode in (1, 2):
+        st, kg, ko, adm = _make(env, L, nbits, seed=21)
+        adm.set_matvec(mode)
+        if ref is None:
+            ref = O.quantized_admm(st, L.lam, L.rho, 3, QP)
+        for t in range(3):
+            adm.round(1)
+            x, z, v, _ = adm.get()
+            assert np.array_equal(x.cpu().numpy(), ref.x[t]), (mode, t)
+            assert np.array_equal(v.cpu().numpy(), ref.v[t]), (mode, t)
+        adm.close()
+    assert ctx.status() == 0
