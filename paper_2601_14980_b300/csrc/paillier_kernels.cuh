@@ -316,8 +316,6 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const 
             A = ly.slot(scratch, tabw + 2 * SW), B = ly.slot(scratch, tabw + 3 * SW),
             C = ly.slot(scratch, tabw + 4 * SW), TT = ly.slot(scratch, tabw + 5 * SW),
             CH = ly.slot(scratch, tabw + 6 * SW);
-  const ModConst<Lh>& M = half ? P.mq : P.mp;
-  const Sched<kMaxSched>& E = half ? P.eq : P.ep;
   for (size_t base = (size_t)blockIdx.x * H; base < count; base += (size_t)gridDim.x * H) {
     size_t e = base + pe;
     const bool valid = e < count;
@@ -327,7 +325,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const 
     const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | (second ? P.kind2 : P.kind)) : P.stream;
     gen_r(X, P.seed, sid, P.e0 + ei, Lh + 2, 2 * Lh);
     make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid && half == 0, status);
-    enc_half<Lh, T>(M, E, X, GM, CH, A, B, C, TT, tab, bsh, g);
+    // the half is uniform per warp; each branch reads its constants at fixed offsets
+    if (half) enc_half<Lh, T>(P.mq, P.eq, X, GM, CH, A, B, C, TT, tab, bsh, g);
+    else enc_half<Lh, T>(P.mp, P.ep, X, GM, CH, A, B, C, TT, tab, bsh, g);
     __syncthreads();
     if (half == 0) {
       // Eq. (gA-C-B) with c_q from the partner group (gl + H) of this CTA
@@ -367,18 +367,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt2(const 
   const Col X = ly.slot(scratch, tabw + 0 * SW), A = ly.slot(scratch, tabw + 1 * SW),
             B = ly.slot(scratch, tabw + 2 * SW), C = ly.slot(scratch, tabw + 3 * SW),
             TT = ly.slot(scratch, tabw + 4 * SW), MH = ly.slot(scratch, tabw + 5 * SW);
-  const ModConst<Lh>& M = half ? P.mq : P.mp;
-  const Sched<kMaxSchedHalf>& E = half ? P.eq : P.ep;
-  const uint32_t* h = half ? P.q : P.p;
-  const uint32_t hnp = half ? P.qnp : P.pnp;
-  const uint32_t* hinvlo = half ? P.qinvlo : P.pinvlo;
-  const uint32_t* hhR = half ? P.hqR : P.hpR;
   for (size_t base = (size_t)blockIdx.x * H; base < count; base += (size_t)gridDim.x * H) {
     size_t e = base + pe;
     const bool valid = e < count;
     if (!valid) e = count - 1;
     for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(ebase + e, j, 2 * Lh)];
-    dec_half<Lh, T>(M, E, h, hnp, hinvlo, hhR, X, MH, A, B, C, TT, tab, bsh, g);
+    if (half) dec_half<Lh, T>(P.mq, P.eq, P.q, P.qnp, P.qinvlo, P.hqR, X, MH, A, B, C, TT, tab, bsh, g);
+    else dec_half<Lh, T>(P.mp, P.ep, P.p, P.pnp, P.pinvlo, P.hpR, X, MH, A, B, C, TT, tab, bsh, g);
     __syncthreads();
     if (half == 0) {
       // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q], m_q from the partner group
