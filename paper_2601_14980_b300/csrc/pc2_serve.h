@@ -15,7 +15,7 @@ namespace pc2 {
 enum { SERVE_ENCRYPT = 1, SERVE_DECRYPT = 2, SERVE_AGGREGATE = 3 };
 // Work-item kinds: the operation and the lanes per element.
 enum { SK_ENC1 = 0, SK_ENC8 = 1, SK_DEC1 = 2, SK_DEC8 = 3, SK_AGG = 4 };
-constexpr int kServeLanesSmall = 8;  // lanes per element for small requests (lower latency)
+constexpr int kServeLanesSmall = 8;  // lanes per CRT half for small requests (halves in parallel: lower latency)
 
 // Lanes per element of an aggregation item: 32 limbs per lane.
 constexpr int serve_agg_lanes(int L2) { return L2 >= 64 ? L2 / 32 : 1; }

@@ -221,9 +221,9 @@ static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl) {
 static double item_cost(int kind, int groups) {
   switch (kind) {
     case SK_ENC1: return 1.0;
-    case SK_ENC8: return 0.2;
+    case SK_ENC8: return 0.1;
     case SK_DEC1: return 0.5;
-    case SK_DEC8: return 0.1;
+    case SK_DEC8: return 0.05;
     default: return 0.002 * groups;
   }
 }
@@ -292,7 +292,7 @@ static int build_step(pc2_server* S, int si, bool* launched) {
       per = (uint32_t)(kThreads / serve_agg_lanes(L2));
     } else if (r->small) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC8 : SK_DEC8;
-      per = kThreads / kServeLanesSmall;
+      per = kThreads / kServeLanesSmall / 2;  // two lane groups (the CRT halves) per element
     } else {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC1 : SK_DEC1;
       per = kThreads;

@@ -7,7 +7,8 @@
 //   aggregate  Definition 1 over `groups` operand vectors: prod_g c_g mod n^2
 //
 // Items of large requests give each element one lane; items of small
-// requests give it eight (shorter latency per element).  Every result is the
+// requests give it eight lanes per CRT half, the two halves in parallel
+// (shorter latency per element).  Every result is the
 // one the per-operation entry points compute (pc2_encrypt, pc2_decrypt,
 // pc2_hom_sum), whatever else runs in the same step.
 #include <cuda_runtime.h>
@@ -99,6 +100,83 @@ __device__ __forceinline__ void serve_decrypt(const ServeKey<Lh>& K, const Serve
   __syncwarp();
 }
 
+// Small requests: the two CRT halves of each element in parallel (the first
+// two warps mod p^2, the last two mod q^2, same elements), recombined after a
+// block barrier; the CTA takes 64 / T elements per item.
+template <int Lh, int T>
+__device__ __forceinline__ void serve_encrypt_split(const ServeKey<Lh>& K, const ServeReq& R, const ServeItem& I,
+                                                    int tabw, uint32_t* cta, uint32_t* bsh_all) {
+  constexpr int L2 = 2 * Lh, G = kThreads / T, H = G / 2;
+  const Grp<T> g;
+  const CtaCols cc{cta, G, (int)threadIdx.x / T};
+  const int half = cc.gl >= H ? 1 : 0, pe = cc.gl - half * H;
+  const Col bsh{bsh_all + cc.gl, G};
+  const int SW = L2 + 4;
+  const Col tab = cc.row(0), X = cc.row(tabw), GM = cc.row(tabw + SW), A = cc.row(tabw + 2 * SW),
+            B = cc.row(tabw + 3 * SW), C = cc.row(tabw + 4 * SW), TT = cc.row(tabw + 5 * SW),
+            CH = cc.row(tabw + 6 * SW);
+  const bool valid = pe < (int)I.count;
+  const size_t idx = I.first + (valid ? (uint32_t)pe : I.count - 1u);
+  gen_r(X, R.seed, R.stream, R.e0 + idx, Lh + 2, L2);
+  gm_u64(GM, A, R.m64[idx], K.enc.nwords, Lh, L2);
+  if (half) enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, X, GM, CH, A, B, C, TT, tab, bsh, g);
+  else enc_half_f<Lh, T>(K.enc.mp, serve_const<Lh>().mp, K.enc.ep, X, GM, CH, A, B, C, TT, tab, bsh, g);
+  __syncthreads();
+  if (!half) {
+    const Col CP = CH, CQ{CH.p + H, CH.s};
+    if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
+    g_copy_param(B, K.enc.pinv2R, Lh);
+    g_mont(C, A, B, K.enc.mq.n, K.enc.mq.np, Lh, TT);
+    g_mul(X, C, Lh, PArr{K.enc.p2}, Lh);
+    uint64_t c = 0;
+    for (int j = 0; j < L2; ++j) {
+      c += (uint64_t)X[j] + (j < Lh ? CP[j] : 0u);
+      X[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    if (valid) write_tiled<T>(R.out, idx, X, L2, g);
+  }
+  __syncthreads();
+}
+
+template <int Lh, int T>
+__device__ __forceinline__ void serve_decrypt_split(const ServeKey<Lh>& K, const ServeReq& R, const ServeItem& I,
+                                                    int tabw, uint32_t* cta, uint32_t* bsh_all) {
+  constexpr int L2 = 2 * Lh, Lp = Lh / 2, G = kThreads / T, H = G / 2;
+  const Grp<T> g;
+  const CtaCols cc{cta, G, (int)threadIdx.x / T};
+  const int half = cc.gl >= H ? 1 : 0, pe = cc.gl - half * H;
+  const Col bsh{bsh_all + cc.gl, G};
+  const int SW = L2 + 4;
+  const Col tab = cc.row(0), X = cc.row(tabw), A = cc.row(tabw + SW), B = cc.row(tabw + 2 * SW),
+            C = cc.row(tabw + 3 * SW), TT = cc.row(tabw + 4 * SW), MH = cc.row(tabw + 5 * SW);
+  const bool valid = pe < (int)I.count;
+  const size_t idx = I.first + (valid ? (uint32_t)pe : I.count - 1u);
+  for (int j = 0; j < L2; ++j) X[j] = R.ct_in[tiled_index(idx, j, L2)];
+  if (half)
+    dec_half_f<Lh, T>(K.dec.mq, serve_const<Lh>().mq, K.dec.eq, K.dec.q, K.dec.qnp, K.dec.qinvlo, K.dec.hqR, X, MH,
+                      A, B, C, TT, tab, bsh, g);
+  else
+    dec_half_f<Lh, T>(K.dec.mp, serve_const<Lh>().mp, K.dec.ep, K.dec.p, K.dec.pnp, K.dec.pinvlo, K.dec.hpR, X, MH,
+                      A, B, C, TT, tab, bsh, g);
+  __syncthreads();
+  if (!half) {
+    const Col MP = MH, MQ{MH.p + H, MH.s};
+    if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{K.dec.q}, Lp);
+    g_copy_param(B, K.dec.pinvqR, Lp);
+    g_mont(C, A, B, K.dec.q, K.dec.qnp, Lp, TT);
+    g_mul(X, C, Lp, PArr{K.dec.p}, Lp);
+    uint64_t c = 0;
+    for (int j = 0; j < Lh; ++j) {
+      c += (uint64_t)X[j] + (j < Lp ? MP[j] : 0u);
+      X[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    if (valid) write_tiled<T>(R.out, idx, X, Lh, g);
+  }
+  __syncthreads();
+}
+
 // prod_g c_g mod n^2: g - 1 Montgomery products, then the fix-up R^groups.
 template <int Lh>
 __device__ __forceinline__ void serve_aggregate(const ServeKey<Lh>& K, const ServeReq& R, const ServeItem& I,
@@ -152,9 +230,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_serve_step(const __grid_constan
     const ServeReq& R = P.reqs[I.req];
     switch (I.kind) {
       case SK_ENC1: serve_encrypt<Lh, 1>(K, R, I, P.tabw, cta, bsh_all, P.status); break;
-      case SK_ENC8: serve_encrypt<Lh, kServeLanesSmall>(K, R, I, P.tabw, cta, bsh_all, P.status); break;
+      case SK_ENC8: serve_encrypt_split<Lh, kServeLanesSmall>(K, R, I, P.tabw, cta, bsh_all); break;
       case SK_DEC1: serve_decrypt<Lh, 1>(K, R, I, P.tabw, cta, bsh_all); break;
-      case SK_DEC8: serve_decrypt<Lh, kServeLanesSmall>(K, R, I, P.tabw, cta, bsh_all); break;
+      case SK_DEC8: serve_decrypt_split<Lh, kServeLanesSmall>(K, R, I, P.tabw, cta, bsh_all); break;
       case SK_AGG: serve_aggregate<Lh>(K, R, I, bsh_all); break;
       default: break;
     }
