@@ -300,10 +300,13 @@ int pc2_batch_tune(pc2_batch* batch, int sample_items, pc2_stream_t stream, int*
  * Mode 0 (continuous batching): a worker thread admits requests in arrival
  * order as arena space frees up (first fit; at most max_active at once),
  * copies their inputs in, and runs steps, each ONE persistent launch over
- * work items of every admitted request (elements of requests of at most
- * small_request elements get 8 lanes each, others one; a step holds about
- * step_budget one-lane encryption items per CTA); two steps are in flight,
- * so requests that arrive while others run join the next step and their work
+ * work items of every admitted request.  Lanes per element are chosen per
+ * step: when the step's encrypt/decrypt elements leave the GPU idle, 8 (or
+ * 2) lanes per CRT half with the two halves in parallel, else one lane;
+ * requests of at most small_request elements always get the 8-lane form.  A
+ * step holds about step_budget one-lane encryption items per CTA; two steps
+ * are in flight, so requests that arrive while others run join the next step
+ * and their work
  * overlaps on the device.  Mode 1 (the plain per-request path): requests run
  * one at a time, in arrival order, through pc2_encrypt / pc2_decrypt /
  * pc2_hom_sum on the context (do not use that context from other threads
@@ -315,7 +318,7 @@ typedef struct {
   size_t arena_bytes;    /* device bytes for the requests' buffers (admission limit) */
   int mode;              /* 0: continuous batching; 1: plain per-request path */
   int max_active;        /* requests admitted at once (0: 256) */
-  size_t small_request;  /* requests of at most this many elements get 8 lanes per element (0: 4096) */
+  size_t small_request;  /* requests of at most this many elements always get 8 lanes per CRT half (0: 4096) */
   double step_budget;    /* work per CTA and step, in one-lane encryption items (0: 1.0) */
 } pc2_server_params;
 

@@ -218,11 +218,14 @@ static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl) {
   return launch_serve_step<64>(P, S->smem, S->grid, sl.st);
 }
 
+// Relative duration of one work item (one-lane encryption item = 1).
 static double item_cost(int kind, int groups) {
   switch (kind) {
     case SK_ENC1: return 1.0;
+    case SK_ENC2: return 0.3;
     case SK_ENC8: return 0.1;
     case SK_DEC1: return 0.5;
+    case SK_DEC2: return 0.15;
     case SK_DEC8: return 0.05;
     default: return 0.002 * groups;
   }
@@ -263,6 +266,15 @@ static int build_step(pc2_server* S, int si, bool* launched) {
   std::vector<std::pair<std::shared_ptr<Req>, size_t>> owners;
   double budget = S->step_budget * S->grid;
   const int L2 = 2 * S->Lh;
+  // lanes per element for this step: as many as the step's encrypt/decrypt
+  // elements can have while still fitting one resident wave of threads
+  size_t pending = 0;
+  for (auto& r : S->active)
+    if (r->state == 1 && r->op != SERVE_AGGREGATE && r->cursor < r->count) pending += r->count - r->cursor;
+  const double cap = (double)S->grid * kThreads;
+  const int lanes = (double)pending * 2 * kServeLanesSmall <= cap ? kServeLanesSmall
+                    : (double)pending * 4 <= cap                ? 2
+                                                                : 1;
   for (auto& r : S->active) {
     if (budget <= 0) break;
     if (r->state != 1 || r->cursor >= r->count) continue;
@@ -290,9 +302,12 @@ static int build_step(pc2_server* S, int si, bool* launched) {
     if (r->op == SERVE_AGGREGATE) {
       kind = SK_AGG;
       per = (uint32_t)(kThreads / serve_agg_lanes(L2));
-    } else if (r->small) {
+    } else if (lanes == kServeLanesSmall || r->small) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC8 : SK_DEC8;
       per = kThreads / kServeLanesSmall / 2;  // two lane groups (the CRT halves) per element
+    } else if (lanes == 2) {
+      kind = r->op == SERVE_ENCRYPT ? SK_ENC2 : SK_DEC2;
+      per = kThreads / 2 / 2;
     } else {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC1 : SK_DEC1;
       per = kThreads;
