@@ -79,11 +79,11 @@ int pc2_ctx_set_window(pc2_ctx* ctx, int w);
  * element and finish sooner). */
 int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes);
 /* Runs the two CRT halves of each element's exponentiations in parallel
- * (one half per two warps of a CTA, recombined after a block barrier) when
- * the lane count is above one: mode 0 automatic (when the doubled lanes still
- * fit one resident wave), 1 never, 2 always.  Results do not change. */
+ * (one half per two warps of a CTA, recombined after a block barrier):
+ * mode 0 automatic (when the doubled lanes still fit one resident wave),
+ * 1 never, 2 always.  Results do not change. */
 int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
-/* Autotuner: times every built lane count x split (where lanes > 1) x window
+/* Autotuner: times every built lane count x split (on, off) x window
  * width (4..6) of key-owner encryption (ops bit 0) and/or decryption (bit 1)
  * on `count` elements (at most two resident waves of them) and records the
  * fastest for calls of the same size class (ceil(log2 count)) on this key

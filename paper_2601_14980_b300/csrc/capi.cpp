@@ -100,7 +100,7 @@ LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
   const bool can_split = op != OP_MATVEC;
   const double cap = (double)ctx->sms * 384.0;  // resident threads of one wave (about 384 per SM)
   auto auto_split = [&](int T) {
-    if (!can_split || T < 2 || ctx->split == 1) return false;
+    if (!can_split || ctx->split == 1) return false;
     return ctx->split == 2 || (double)count * 2 * T <= cap;
   };
   if (ctx->lanes)
@@ -117,8 +117,8 @@ LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
   int best_lanes = 0;
   for (int i = 0; i < n; ++i) {
     for (int s = 0; s < 2; ++s) {
-      if (s && (!can_split || set[i] < 2 || ctx->split == 1)) continue;
-      if (!s && ctx->split == 2 && set[i] > 1 && can_split) continue;
+      if (s && (!can_split || ctx->split == 1)) continue;
+      if (!s && ctx->split == 2 && can_split) continue;
       const int le = set[i] * (s ? 2 : 1);
       if ((double)count * le > cap) continue;
       if (le > best_lanes || (le == best_lanes && s)) {
@@ -163,9 +163,7 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->mwords = mw ? Lh : 2;
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
-    if constexpr (T > 1)
-      if (cfg.split)
-        return launch_enc_crt2<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
+    if (cfg.split) return launch_enc_crt2<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
     return launch_enc_crt<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
   });
 }
@@ -192,10 +190,8 @@ static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, 
   P->base2 = base2;
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
-    if constexpr (T > 1)
-      if (cfg.split)  // both vectors in one launch
-        return launch_enc_crt2<Lh, T>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st,
-                                      base);
+    if (cfg.split)  // both vectors in one launch
+      return launch_enc_crt2<Lh, T>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
     if (split >= count)
       return launch_enc_crt<Lh, T>(*P, m64, nullptr, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
     // the one-vector kernel: the two vectors one after the other
@@ -251,8 +247,7 @@ static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
   if (!P) return rc;
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
-    if constexpr (T > 1)
-      if (cfg.split) return launch_dec_crt2<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
+    if (cfg.split) return launch_dec_crt2<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
     return launch_dec_crt<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
   });
 }
@@ -469,7 +464,7 @@ int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_st
     float best = 1e30f;
     std::tuple<int, int, int> pick{set[0], 0, 0};
     for (int i = 0; i < nl && rc == PC2_OK; ++i) {
-      for (int s = 0; s < (set[i] > 1 ? 2 : 1) && rc == PC2_OK; ++s) {
+      for (int s = 0; s < 2 && rc == PC2_OK; ++s) {
         for (int w = 4; w <= kMaxWin && rc == PC2_OK; ++w) {
           ctx->lanes = set[i];
           ctx->split = s ? 2 : 1;

@@ -19,4 +19,7 @@ template int launch_dec_crt2<32, 4>(const DecParams<32>&, const uint32_t*, size_
 template int launch_enc_crt2<32, 8>(const EncCrtParams<32>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
 template int launch_dec_crt2<32, 8>(const DecParams<32>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
 
+template int launch_enc_crt2<32, 1>(const EncCrtParams<32>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
+template int launch_dec_crt2<32, 1>(const DecParams<32>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
+
 }  // namespace pc2

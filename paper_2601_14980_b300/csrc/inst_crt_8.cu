@@ -15,4 +15,7 @@ template int launch_dec_crt2<8, 2>(const DecParams<8>&, const uint32_t*, size_t,
 template int launch_enc_crt2<8, 4>(const EncCrtParams<8>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
 template int launch_dec_crt2<8, 4>(const DecParams<8>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
 
+template int launch_enc_crt2<8, 1>(const EncCrtParams<8>&, const uint64_t*, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int*, int, cudaStream_t, size_t);
+template int launch_dec_crt2<8, 1>(const DecParams<8>&, const uint32_t*, size_t, uint32_t*, ScratchFn, void*, int, cudaStream_t, size_t);
+
 }  // namespace pc2

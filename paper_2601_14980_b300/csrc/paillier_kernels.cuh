@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
 // warps) works mod p^2 and the second half mod q^2 on the same elements, and
 // the recombination follows a block barrier.  Each warp runs one exponent's
 // schedule, so control flow stays uniform.  Halves the time per element when
-// the batch leaves most of the GPU idle (small batches; T > 1).
+// the batch leaves most of the GPU idle (small batches; any T, one lane per
+// half included).
 // Encryption also takes a second vector in the same launch: elements
 // e >= P.split use r-stream kind2, counter e0 + (e - split) and tiled output
 // position base2 + (e - split).
@@ -302,7 +303,6 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const 
                                                       const uint32_t* __restrict__ mwide, size_t count,
                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
                                                       int tabw, int* status, size_t base_out) {
-  static_assert(T > 1, "one CRT half per two warps needs lane groups");
   extern __shared__ uint32_t bsh_all[];
   const Grp<T> g;
   const Layout ly(T);
@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt2(const 
                                                       const uint32_t* __restrict__ ct, size_t count,
                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
                                                       int tabw, size_t ebase) {
-  static_assert(T > 1, "one CRT half per two warps needs lane groups");
   constexpr int Lp = Lh / 2;
   extern __shared__ uint32_t bsh_all[];
   const Grp<T> g;

@@ -15,7 +15,8 @@ namespace pc2 {
 enum { SERVE_ENCRYPT = 1, SERVE_DECRYPT = 2, SERVE_AGGREGATE = 3 };
 // Work-item kinds: the operation and the lanes per element (1: one lane;
 // 2, 8: that many lanes per CRT half, the two halves in parallel).
-enum { SK_ENC1 = 0, SK_ENC8 = 1, SK_DEC1 = 2, SK_DEC8 = 3, SK_AGG = 4, SK_ENC2 = 5, SK_DEC2 = 6 };
+enum { SK_ENC1 = 0, SK_ENC8 = 1, SK_DEC1 = 2, SK_DEC8 = 3, SK_AGG = 4, SK_ENC2 = 5, SK_DEC2 = 6, SK_ENC1S = 7,
+       SK_DEC1S = 8 };  // *1S: one lane per CRT half, halves in parallel
 constexpr int kServeLanesSmall = 8;  // lanes per CRT half for small requests (halves in parallel: lower latency)
 
 // Lanes per element of an aggregation item: 32 limbs per lane.

@@ -222,9 +222,11 @@ static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl) {
 static double item_cost(int kind, int groups) {
   switch (kind) {
     case SK_ENC1: return 1.0;
+    case SK_ENC1S: return 0.5;
     case SK_ENC2: return 0.3;
     case SK_ENC8: return 0.1;
     case SK_DEC1: return 0.5;
+    case SK_DEC1S: return 0.25;
     case SK_DEC2: return 0.15;
     case SK_DEC8: return 0.05;
     default: return 0.002 * groups;
@@ -272,9 +274,11 @@ static int build_step(pc2_server* S, int si, bool* launched) {
   for (auto& r : S->active)
     if (r->state == 1 && r->op != SERVE_AGGREGATE && r->cursor < r->count) pending += r->count - r->cursor;
   const double cap = (double)S->grid * kThreads;
+  // lanes per CRT half with the halves split (0: one lane per element, not split)
   const int lanes = (double)pending * 2 * kServeLanesSmall <= cap ? kServeLanesSmall
                     : (double)pending * 4 <= cap                ? 2
-                                                                : 1;
+                    : (double)pending * 2 <= cap                ? 1
+                                                                : 0;
   for (auto& r : S->active) {
     if (budget <= 0) break;
     if (r->state != 1 || r->cursor >= r->count) continue;
@@ -308,6 +312,9 @@ static int build_step(pc2_server* S, int si, bool* launched) {
     } else if (lanes == 2) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC2 : SK_DEC2;
       per = kThreads / 2 / 2;
+    } else if (lanes == 1) {
+      kind = r->op == SERVE_ENCRYPT ? SK_ENC1S : SK_DEC1S;
+      per = kThreads / 2;
     } else {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC1 : SK_DEC1;
       per = kThreads;

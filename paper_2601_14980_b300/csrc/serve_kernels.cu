@@ -7,7 +7,7 @@
 //   aggregate  Definition 1 over `groups` operand vectors: prod_g c_g mod n^2
 //
 // Each step gives every element one lane when the step's work fills the GPU,
-// else two or eight lanes per CRT half with the two halves in parallel
+// else one, two or eight lanes per CRT half with the two halves in parallel
 // (shorter latency per element when the GPU would idle).  Every result is the
 // one the per-operation entry points compute (pc2_encrypt, pc2_decrypt,
 // pc2_hom_sum), whatever else runs in the same step.
@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_serve_step(const __grid_constan
       case SK_AGG: serve_aggregate<Lh>(K, R, I, bsh_all); break;
       case SK_ENC2: serve_encrypt_split<Lh, 2>(K, R, I, P.tabw, cta, bsh_all); break;
       case SK_DEC2: serve_decrypt_split<Lh, 2>(K, R, I, P.tabw, cta, bsh_all); break;
+      case SK_ENC1S: serve_encrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all); break;
+      case SK_DEC1S: serve_decrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all); break;
       default: break;
     }
   }

@@ -436,7 +436,7 @@ _ctx_set_split = _sig("pc2_ctx_set_split", [_vp, _i])
 
 
 def set_split(ctx: Context, mode: int):
-    """CRT halves in parallel: 0 automatic, 1 never, 2 whenever lanes > 1."""
+    """CRT halves in parallel: 0 automatic, 1 never, 2 always."""
     _check(_ctx_set_split(ctx.h, mode), "pc2_ctx_set_split")
 
 

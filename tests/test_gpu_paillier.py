@@ -153,8 +153,6 @@ def test_lanes_and_windows_bit_identical(env, nbits):
     L2 = 2 * kg.limbs
     try:
         for lanes, w, split in [(l, w, s) for l in (1, 2, 4, 8) for w in (0, 4, 6) for s in (1, 2)]:
-            if lanes == 1 and split == 2:
-                continue
             pc2.set_lanes(ctx, lanes)
             pc2.set_split(ctx, split)      # 1: halves one after the other, 2: in parallel
             ctx.set_window(w)
