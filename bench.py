@@ -196,6 +196,50 @@ def run_admm(dev, rounds: int = 5):
             "mse_private": out["mse"], "mse_plaintext": out["mse_plain"]}
 
 
+def run_admm_full(dev, rounds: int = 2):
+    """Full-scale private ADMM: 256 x 256 image-like LASSO (N = 65536, 16 edge
+    nodes of 4096, A of N/4 x N), 3072-bit n, lambda 0.005, rho 1.  Seconds per
+    round of the batched path (round 1 eager, then the captured graph) and of
+    the per-node path."""
+    import numpy as np
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+    from paper_2601_14980_b300 import workloads as W
+
+    x0, sizes, A, y = W.lasso_large_data(device=dev)
+    rho, lam = 1.0, 0.005
+    alphas, bbars = [], []
+    for Ak in A:
+        B = torch.linalg.inv(Ak.T @ Ak + rho * torch.eye(Ak.shape[1], dtype=torch.float64, device=Ak.device))
+        alphas.append(B @ (Ak.T @ y))
+        bbars.append((rho * B).reshape(-1))
+    del A
+    alpha, Bbar = torch.cat(alphas), torch.cat(bbars)
+    del alphas, bbars
+    ctx = pc2.Context(dev)
+    key = pc2.Key.generate(3072, 2028)
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, per_node in (("batched", False), ("per_node", True)):
+        adm = pc2.Admm(ctx, key, sizes, alpha, Bbar, lam, rho, -8.0, 8.0, 24, 77, per_node=per_node)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        adm.round(rounds)
+        b.record(st)
+        b.synchronize()
+        out[name] = a.elapsed_time(b) / 1e3 / rounds
+        if name == "batched":
+            out["mse"] = float(np.mean((adm.get()[0].cpu().numpy() - x0) ** 2))
+            out["matvec"] = adm.info()
+        adm.close()
+    return {"workload": "lasso_large: N=65536 (256x256, 5%% DCT nonzeros), 16 edge nodes, A %dx%d, 3072-bit n, "
+                        "%d rounds" % (len(y), len(x0), rounds),
+            "s_per_iter_batched": out["batched"], "s_per_iter_per_node": out["per_node"],
+            "batched_speedup": out["per_node"] / out["batched"], "mse_after_rounds": out["mse"],
+            "matvec": out["matvec"], "status": ctx.status()}
+
+
 def run_batch(dev, rounds: int = 1, per_node_rounds: int = 1, tune: bool = True):
     """Batching form: 64 edge nodes, sizes log-uniform in [256, 65536], keys of
     1024/2048/3072 bits (one per size, nodes assigned in turn), orthonormal
@@ -452,6 +496,7 @@ def run_gpu(args):
         "admm": None if args.no_admm else run_admm(dev),
         "batch": None if args.no_batch else run_batch(dev, args.batch_rounds),
         "serve": None if args.no_serve else run_serve(dev),
+        "admm_full": run_admm_full(dev) if args.admm_full else None,
     }
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
@@ -484,6 +529,7 @@ def main():
     ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--admm-full", action="store_true", help="also time the full-scale 3072-bit ADMM (about 2 min)")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
     ap.add_argument("--groups", type=int, default=GROUPS)

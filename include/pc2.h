@@ -301,9 +301,11 @@ int pc2_batch_tune(pc2_batch* batch, int sample_items, pc2_stream_t stream, int*
  * order as arena space frees up (first fit; at most max_active at once),
  * copies their inputs in, and runs steps, each ONE persistent launch over
  * work items of every admitted request.  Lanes per element are chosen per
- * step: when the step's encrypt/decrypt elements leave the GPU idle, 8 (or
- * 2) lanes per CRT half with the two halves in parallel, else one lane;
- * requests of at most small_request elements always get the 8-lane form.  A
+ * request and step: every encrypt/decrypt request starts at 8 lanes per CRT
+ * half with the two halves in parallel, and while the step's threads exceed
+ * one resident wave the request with the largest demand steps down to 2 and
+ * 1 lanes per half, then one lane per element; requests of at most
+ * small_request elements keep the 8-lane form.  A
  * step holds about step_budget one-lane encryption items per CTA; two steps
  * are in flight, so requests that arrive while others run join the next step
  * and their work

@@ -268,18 +268,41 @@ static int build_step(pc2_server* S, int si, bool* launched) {
   std::vector<std::pair<std::shared_ptr<Req>, size_t>> owners;
   double budget = S->step_budget * S->grid;
   const int L2 = 2 * S->Lh;
-  // lanes per element for this step: as many as the step's encrypt/decrypt
-  // elements can have while still fitting one resident wave of threads
-  size_t pending = 0;
-  for (auto& r : S->active)
-    if (r->state == 1 && r->op != SERVE_AGGREGATE && r->cursor < r->count) pending += r->count - r->cursor;
-  const double cap = (double)S->grid * kThreads;
-  // lanes per CRT half with the halves split (0: one lane per element, not split)
-  const int lanes = (double)pending * 2 * kServeLanesSmall <= cap ? kServeLanesSmall
-                    : (double)pending * 4 <= cap                ? 2
-                    : (double)pending * 2 <= cap                ? 1
-                                                                : 0;
-  for (auto& r : S->active) {
+  // Lanes per element for each request of this step: start every request at
+  // 8 lanes per CRT half (16 per element) and, while the step's threads do
+  // not fit one resident wave, move the request with the largest demand down
+  // to 2 lanes per half, 1 lane per half, then one lane per element; small
+  // requests keep the 16.
+  static const int kLaneSteps[4] = {2 * kServeLanesSmall, 4, 2, 1};
+  std::vector<int> lvl(S->active.size(), 0);
+  {
+    const double cap = (double)S->grid * kThreads;
+    auto demand = [&](size_t i) {
+      const auto& r = S->active[i];
+      if (r->state != 1 || r->op == SERVE_AGGREGATE || r->cursor >= r->count) return 0.0;
+      return (double)(r->count - r->cursor) * kLaneSteps[lvl[i]];
+    };
+    double total = 0;
+    for (size_t i = 0; i < lvl.size(); ++i) total += demand(i);
+    while (total > cap) {
+      size_t arg = lvl.size();
+      double worst = 0;
+      for (size_t i = 0; i < lvl.size(); ++i) {
+        if (lvl[i] == 3 || S->active[i]->small) continue;
+        const double d = demand(i);
+        if (d > worst) {
+          worst = d;
+          arg = i;
+        }
+      }
+      if (arg == lvl.size()) break;
+      total -= worst;
+      ++lvl[arg];
+      total += demand(arg);
+    }
+  }
+  for (size_t ai = 0; ai < S->active.size(); ++ai) {
+    auto& r = S->active[ai];
     if (budget <= 0) break;
     if (r->state != 1 || r->cursor >= r->count) continue;
     const uint32_t ri = (uint32_t)reqs.size();
@@ -306,13 +329,13 @@ static int build_step(pc2_server* S, int si, bool* launched) {
     if (r->op == SERVE_AGGREGATE) {
       kind = SK_AGG;
       per = (uint32_t)(kThreads / serve_agg_lanes(L2));
-    } else if (lanes == kServeLanesSmall || r->small) {
+    } else if (lvl[ai] == 0 || r->small) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC8 : SK_DEC8;
       per = kThreads / kServeLanesSmall / 2;  // two lane groups (the CRT halves) per element
-    } else if (lanes == 2) {
+    } else if (lvl[ai] == 1) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC2 : SK_DEC2;
       per = kThreads / 2 / 2;
-    } else if (lanes == 1) {
+    } else if (lvl[ai] == 2) {
       kind = r->op == SERVE_ENCRYPT ? SK_ENC1S : SK_DEC1S;
       per = kThreads / 2;
     } else {
