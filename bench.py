@@ -357,8 +357,10 @@ def run_serve(dev, rates=(5.0, 15.0, 30.0, 45.0, 60.0), seconds: float = 4.0, se
             span = max(s + l for s, l in zip(sub, lats)) - t0
             st = srv.stats()
             srv.close()
+            worst = sorted(range(n), key=lambda i: -lats[i])[:3]
             res[name] = {"p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
-                         "ciphertexts_per_s": int(counts.sum()) / span, "makespan_s": span, "steps": st["steps"]}
+                         "ciphertexts_per_s": int(counts.sum()) / span, "makespan_s": span, "steps": st["steps"],
+                         "slowest": [{"op": int(ops[i]), "count": int(counts[i]), "latency_s": lats[i]} for i in worst]}
         points.append(res)
     return {"workload": "serving: Poisson arrivals from 256 edge nodes, 2048-bit n, sizes log-uniform [64, 32768], "
                         "encrypt/decrypt/aggregate(2..16) in equal shares, %.0f s per rate" % seconds,

@@ -73,8 +73,9 @@ struct ServeParams {
   int* status;
 };
 
+// one_lane_split: run the SK_ENC1S / SK_DEC1S items (k_serve_step_s1) instead of the others.
 template <int Lh>
-int launch_serve_step(const ServeParams& P, size_t smem, int grid, cudaStream_t st);
+int launch_serve_step(const ServeParams& P, size_t smem, int grid, cudaStream_t st, bool one_lane_split);
 // Copies a key's one-lane moduli to constant memory (synchronises `st`); the
 // constant block is shared by every server of this key size in the process.
 template <int Lh>

@@ -203,7 +203,7 @@ static int serve_setup(pc2_server* S) {
 static std::mutex g_const_mu;
 static const pc2_server* g_const_owner[2] = {nullptr, nullptr};
 
-static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl) {
+static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl, bool one_lane_split) {
   {
     std::lock_guard<std::mutex> g(g_const_mu);
     const pc2_server*& own = g_const_owner[S->Lh == 16 ? 0 : 1];
@@ -214,8 +214,8 @@ static int launch_step(pc2_server* S, const ServeParams& P, Slot& sl) {
       own = S;
     }
   }
-  if (S->Lh == 16) return launch_serve_step<16>(P, S->smem, S->grid, sl.st);
-  return launch_serve_step<64>(P, S->smem, S->grid, sl.st);
+  if (S->Lh == 16) return launch_serve_step<16>(P, S->smem, S->grid, sl.st, one_lane_split);
+  return launch_serve_step<64>(P, S->smem, S->grid, sl.st, one_lane_split);
 }
 
 // Relative duration of one work item (one-lane encryption item = 1).
@@ -354,12 +354,18 @@ static int build_step(pc2_server* S, int si, bool* launched) {
     owners.emplace_back(r, n_items);
   }
   if (its.empty()) return PC2_OK;
+  // one-lane-per-half items run in their own kernel, after the others
+  const size_t n_main = (size_t)(std::stable_partition(its.begin(), its.end(),
+                                                       [](const ServeItem& x) {
+                                                         return x.kind != SK_ENC1S && x.kind != SK_DEC1S;
+                                                       }) -
+                                 its.begin());
   if (!ensure_slot_cap(sl, reqs.size(), its.size())) return PC2_ENOMEM;
   std::memcpy(sl.h_reqs, reqs.data(), reqs.size() * sizeof(ServeReq));
   std::memcpy(sl.h_items, its.data(), its.size() * sizeof(ServeItem));
   if (cudaMemcpyAsync(sl.d_reqs, sl.h_reqs, reqs.size() * sizeof(ServeReq), cudaMemcpyHostToDevice, sl.st) ||
       cudaMemcpyAsync(sl.d_items, sl.h_items, its.size() * sizeof(ServeItem), cudaMemcpyHostToDevice, sl.st) ||
-      cudaMemsetAsync(sl.d_next, 0, 4, sl.st))
+      cudaMemsetAsync(sl.d_next, 0, 8, sl.st))
     return PC2_ECUDA;
   ServeParams P;
   std::memset(&P, 0, sizeof(P));
@@ -373,8 +379,19 @@ static int build_step(pc2_server* S, int si, bool* launched) {
   P.scratch = S->scratch + (size_t)si * S->grid * S->cta_words;
   P.cta_words = S->cta_words;
   P.status = S->ctx->status;
-  int rc = launch_step(S, P, sl);
-  if (rc) return rc;
+  int rc = PC2_OK;
+  if (n_main) {
+    P.nitems = (uint32_t)n_main;
+    rc = launch_step(S, P, sl, false);
+    if (rc) return rc;
+  }
+  if (n_main < its.size()) {
+    P.items = sl.d_items + n_main;
+    P.nitems = (uint32_t)(its.size() - n_main);
+    P.next = sl.d_next + 1;
+    rc = launch_step(S, P, sl, true);
+    if (rc) return rc;
+  }
   if (cudaEventRecord(sl.ev, sl.st) != cudaSuccess) return PC2_ECUDA;
   sl.owners = std::move(owners);
   sl.busy = true;
@@ -581,7 +598,7 @@ int pc2_server_create(pc2_ctx* ctx, const pc2_key* key, const pc2_server_params*
   for (auto& sl : S->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&sl.d_next, 4) != cudaSuccess)
+        cudaMalloc(&sl.d_next, 8) != cudaSuccess)
       return PC2_ECUDA;
   }
   if (cudaStreamCreateWithFlags(&S->copy_in, cudaStreamNonBlocking) != cudaSuccess ||

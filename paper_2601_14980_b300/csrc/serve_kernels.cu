@@ -236,10 +236,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_serve_step(const __grid_constan
       case SK_AGG: serve_aggregate<Lh>(K, R, I, bsh_all); break;
       case SK_ENC2: serve_encrypt_split<Lh, 2>(K, R, I, P.tabw, cta, bsh_all); break;
       case SK_DEC2: serve_decrypt_split<Lh, 2>(K, R, I, P.tabw, cta, bsh_all); break;
-      case SK_ENC1S: serve_encrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all); break;
-      case SK_DEC1S: serve_decrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all); break;
       default: break;
     }
+  }
+}
+
+// The one-lane-per-half items (SK_ENC1S, SK_DEC1S) in a kernel of their own:
+// inside k_serve_step their two 64-limb copies of the exponentiation next to
+// the other item kinds raised the register pressure of the whole kernel into
+// heavy spilling.
+template <int Lh>
+__global__ void __launch_bounds__(kThreads, 3) k_serve_step_s1(const __grid_constant__ ServeParams P) {
+  extern __shared__ uint32_t bsh_all[];
+  __shared__ uint32_t s_item;
+  const ServeKey<Lh>& K = *static_cast<const ServeKey<Lh>*>(P.key);
+  uint32_t* cta = P.scratch + (size_t)blockIdx.x * P.cta_words;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(P.next, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    __syncthreads();
+    if (it >= P.nitems) break;
+    const ServeItem I = P.items[it];
+    const ServeReq& R = P.reqs[I.req];
+    if (I.kind == SK_ENC1S) serve_encrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all);
+    else if (I.kind == SK_DEC1S) serve_decrypt_split<Lh, 1>(K, R, I, P.tabw, cta, bsh_all);
   }
 }
 
@@ -263,13 +284,20 @@ int serve_set_const(const ServeConst<Lh>* d_const, cudaStream_t st) {
 }
 
 template <int Lh>
-int launch_serve_step(const ServeParams& P, size_t smem, int grid, cudaStream_t st) {
-  k_serve_step<Lh><<<grid, kThreads, smem, st>>>(P);
+int launch_serve_step(const ServeParams& P, size_t smem, int grid, cudaStream_t st, bool one_lane_split) {
+  if (one_lane_split) {
+    if (cudaFuncSetAttribute(k_serve_step_s1<Lh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return PC2_ECUDA;
+    k_serve_step_s1<Lh><<<grid, kThreads, smem, st>>>(P);
+  } else {
+    k_serve_step<Lh><<<grid, kThreads, smem, st>>>(P);
+  }
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
-template int launch_serve_step<16>(const ServeParams&, size_t, int, cudaStream_t);
-template int launch_serve_step<64>(const ServeParams&, size_t, int, cudaStream_t);
+template int launch_serve_step<16>(const ServeParams&, size_t, int, cudaStream_t, bool);
+template int launch_serve_step<64>(const ServeParams&, size_t, int, cudaStream_t, bool);
 template int serve_set_const<16>(const ServeConst<16>*, cudaStream_t);
 template int serve_set_const<64>(const ServeConst<64>*, cudaStream_t);
 template int serve_blocks_per_sm<16>(size_t);
