@@ -164,6 +164,31 @@ int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const u
 int pc2_quantize(pc2_ctx* ctx, const double* d_u, size_t n, double zmin, double zmax, int log2_scale, int gamma,
                  int negate, uint64_t* d_q, pc2_stream_t stream);
 
+/* Inverse of pc2_quantize: u = q / S + zmin (gamma 2) or q / S^2 + zmin
+ * (gamma 1), IEEE double (exact whenever u needs at most 53 significant bits,
+ * as the quantizer's outputs do).  d_q: n uint64; d_u: n doubles. */
+int pc2_dequantize(pc2_ctx* ctx, const uint64_t* d_q, size_t n, double zmin, int log2_scale, int gamma, double* d_u,
+                   pc2_stream_t stream);
+/* The exact decode of Theorem 1 for rows of an encrypted matvec (Eq. (itq2)
+ * decrypted): with mS = zmin S (an integer),
+ *   x_i = fl(D_i + mS S + 2 mS brow_i + mS asum_i + 2 mS^2 nk_i) / S^2,
+ * D_i the decrypted integers (tiled, `limbs` words each, < 2^128), brow_i =
+ * sum_j b_ij over the row, asum_i = sum_j a_j over its block (a_j = Gamma2(z_j)
+ * + Gamma2(-v_j)), nk_i the block's column count.  PC2_ST_RANGE when a D_i is
+ * 2^128 or more or the sum leaves 64 bits. */
+int pc2_decode_matvec(pc2_ctx* ctx, const uint32_t* d_D, int limbs, size_t n, const long long* d_brow,
+                      const unsigned long long* d_asum, const int* d_nk, double zmin, int log2_scale, double* d_x,
+                      pc2_stream_t stream);
+
+/* ---- encrypted matrix-vector product ----------------------------------- *
+ * Eq. (itq2) on one n x n block: out_i = alpha_i (+) sum_j K_ij (x) s_j =
+ * alpha_i * prod_j s_j^{K_ij} mod n^2, by the bucket method of the ADMM
+ * round (same kernels, same window choice).  d_alpha, d_s, d_out: n tiled
+ * ciphertexts; d_K: n*n uint32, row-major, every K_ij < 2^kbits (kbits 1..32,
+ * 0 = 32; higher bits are ignored).  Scratch from the context. */
+int pc2_hom_matvec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_alpha, const uint32_t* d_s, const uint32_t* d_K,
+                   size_t n, int kbits, uint32_t* d_out, pc2_stream_t stream);
+
 /* ---- 3P-ADMM-PC2 on one GPU (Algorithm 1) ------------------------------- *
  * The K edge nodes are segments of device vectors (node k owns elements
  * [N_0 + ... + N_{k-1}, ... + N_k)).  Inputs are the edge nodes' set-up
@@ -209,6 +234,10 @@ int pc2_admm_get(pc2_admm* admm, double* d_x, double* d_z, double* d_v, uint32_t
 /* Restores a checkpoint: x, z, v and the next round number (>= 1). */
 int pc2_admm_set(pc2_admm* admm, const double* d_x, const double* d_z, const double* d_v, uint32_t round,
                  pc2_stream_t stream);
+/* Checkpoint to / from host memory: x, z, v (N doubles each) and the next
+ * round number (synchronises the device). */
+int pc2_admm_save(pc2_admm* admm, double* h_x, double* h_z, double* h_v, uint32_t* h_round);
+int pc2_admm_load(pc2_admm* admm, const double* h_x, const double* h_z, const double* h_v, uint32_t round);
 /* Device pointers of the last round's ciphertexts (tiled) and decrypted integers, and N. */
 int pc2_admm_buffers(pc2_admm* admm, const uint32_t** zhat, const uint32_t** vhat, const uint32_t** xhat,
                      const uint32_t** alpha_hat, const uint32_t** D, int* N);

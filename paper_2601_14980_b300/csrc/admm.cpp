@@ -164,6 +164,85 @@ static int dispatch_to_mont(pc2_admm* A, cudaStream_t st) {
   }
 }
 
+// Eq. (itq2) on one n x n block outside an ADMM object: K_ij < 2^kbits, scratch
+// from the context (Montgomery form of s, tile tables, window products, kernel
+// scratch), same kernels and choices as the round's matvec.
+template <int L2, int T>
+static int block_matvec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* alpha, const uint32_t* s, const uint32_t* K,
+                        int n, int kbits, uint32_t* out, cudaStream_t st) {
+  const int G = kThreads / T, ntiles = (n + G - 1) / G;
+  // bucket window: fewest products per row, nwin * (n + 2 (2^c - 1) + c + 1)
+  int c = 1, nwin = kbits;
+  double best = 1e300;
+  for (int cc = 1; cc <= 8; ++cc) {
+    const int nw = (kbits + cc - 1) / cc;
+    const double cost = (double)nw * (n + 2.0 * ((1 << cc) - 1) + cc + 1);
+    if (cost < best) {
+      best = cost;
+      c = cc;
+      nwin = nw;
+    }
+  }
+  std::unique_ptr<MatvecParams<L2>> P(new (std::nothrow) MatvecParams<L2>);
+  std::unique_ptr<ModConst<L2>> M(new (std::nothrow) ModConst<L2>);
+  if (!P || !M) return PC2_ENOMEM;
+  std::memset(P.get(), 0, sizeof(MatvecParams<L2>));
+  fill_mod(*M, key->n2);
+  P->m = *M;
+  P->c = c;
+  P->nwin = nwin;
+  P->ntiles = ntiles;
+  const int cap = matvec_win_grid<L2, T>(1 << 30, ctx->sms);
+  if (cap < 1) return PC2_ECUDA;
+  const bool win_par = nwin > 1 && 2 * ntiles < cap;
+  const int grid = win_par ? std::min(ntiles * nwin, cap) : matvec_grid<L2, T>(ntiles, ctx->sms);
+  if (grid < 1) return PC2_ECUDA;
+  // scratch layout (words, 64-word aligned): smont | tables | window products | kernel scratch
+  auto up = [](size_t w) { return (w + 63) / 64 * 64; };
+  const size_t w_smont = up((size_t)n * L2), w_tab = up(4 + 2 * (size_t)ntiles + 2);
+  const size_t w_part = win_par ? up(pc2_tiled_words((size_t)n * nwin, L2)) : 0;
+  const size_t w_kern = matvec_scratch_words<L2, T>(c, grid);
+  uint32_t* base = ctx_scratch_get(ctx, (w_smont + w_tab + w_part + w_kern) * 4);
+  if (!base) return PC2_ENOMEM;
+  uint32_t* smont = base;
+  uint32_t* tab = base + w_smont;
+  uint32_t* part = tab + w_tab;
+  uint32_t* kscr = part + w_part;
+  // tables: node_off {0, n}, boff {0} (64-bit), tile_node, tile_row0
+  std::vector<int> ht(w_tab, 0);
+  ht[0] = 0;
+  ht[1] = n;
+  long long* boff_h = reinterpret_cast<long long*>(&ht[2]);
+  *boff_h = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    ht[4 + t] = 0;
+    ht[4 + ntiles + t] = t * G;
+  }
+  if (cudaMemcpyAsync(tab, ht.data(), w_tab * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) return PC2_ECUDA;
+  const int* node_off = reinterpret_cast<const int*>(tab);
+  const long long* boff = reinterpret_cast<const long long*>(tab + 2);
+  const int* tile_node = reinterpret_cast<const int*>(tab + 4);
+  const int* tile_row0 = reinterpret_cast<const int*>(tab + 4 + ntiles);
+  int rc = launch_to_mont_rows<L2, lanes_for(L2)>(*M, s, n, smont, ctx->sms, st);
+  if (rc) return rc;
+  if (win_par)
+    return launch_matvec_win<L2, T>(*P, alpha, smont, K, boff, node_off, tile_node, tile_row0, n, part, out, kscr,
+                                    grid, ctx->sms, st);
+  return launch_matvec<L2, T>(*P, alpha, smont, K, boff, node_off, tile_node, tile_row0, out, kscr, grid, st);
+}
+
+template <int L2>
+static int block_matvec_any(pc2_ctx* ctx, const pc2_key* key, const uint32_t* alpha, const uint32_t* s,
+                            const uint32_t* K, int n, int kbits, uint32_t* out, cudaStream_t st) {
+  switch (pick_config(ctx, OP_MATVEC, L2, (size_t)n).T) {
+    case 1: if constexpr (L2 <= 64) return block_matvec<L2, 1>(ctx, key, alpha, s, K, n, kbits, out, st); break;
+    case 2: if constexpr (L2 <= 64) return block_matvec<L2, 2>(ctx, key, alpha, s, K, n, kbits, out, st); break;
+    case 4: return block_matvec<L2, 4>(ctx, key, alpha, s, K, n, kbits, out, st);
+    case 8: if constexpr (L2 >= 32) return block_matvec<L2, 8>(ctx, key, alpha, s, K, n, kbits, out, st); break;
+  }
+  return PC2_EUNSUPPORTED;
+}
+
 #define PC2_TRY(x)            \
   do {                        \
     const int rc_ = (x);      \
@@ -438,6 +517,67 @@ int pc2_admm_buffers(pc2_admm* A, const uint32_t** zhat, const uint32_t** vhat, 
   if (alpha_hat) *alpha_hat = A->alpha_hat.p;
   if (D) *D = A->D.p;
   if (N) *N = A->N;
+  return PC2_OK;
+}
+
+int pc2_dequantize(pc2_ctx* ctx, const uint64_t* d_q, size_t n, double zmin, int log2_scale, int gamma, double* d_u,
+                   pc2_stream_t stream) {
+  if (!ctx || (n && (!d_q || !d_u)) || (gamma != 1 && gamma != 2) || log2_scale < 0 || log2_scale > 40)
+    return PC2_EINVAL;
+  if (!n) return PC2_OK;
+  const double inv = std::ldexp(1.0, -(gamma == 1 ? 2 : 1) * log2_scale);
+  return launch_dequantize(d_q, n, zmin, inv, d_u, ctx->sms, (cudaStream_t)stream);
+}
+
+int pc2_decode_matvec(pc2_ctx* ctx, const uint32_t* d_D, int limbs, size_t n, const long long* d_brow,
+                      const unsigned long long* d_asum, const int* d_nk, double zmin, int log2_scale, double* d_x,
+                      pc2_stream_t stream) {
+  if (!ctx || limbs < 4 || limbs % 4 || log2_scale < 1 || log2_scale > 30 ||
+      (n && (!d_D || !d_brow || !d_asum || !d_nk || !d_x)))
+    return PC2_EINVAL;
+  if (!n) return PC2_OK;
+  const long long S = 1LL << log2_scale;
+  const double ms = zmin * (double)S;
+  if (ms != std::floor(ms) || std::fabs(ms) > 9.0e15) return PC2_EINVAL;  // zmin * S must be an integer
+  return launch_decode_matvec(d_D, limbs, n, d_brow, d_asum, d_nk, (long long)ms, S, std::ldexp(1.0, -2 * log2_scale),
+                              d_x, ctx->status, ctx->sms, (cudaStream_t)stream);
+}
+
+int pc2_hom_matvec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_alpha, const uint32_t* d_s, const uint32_t* d_K,
+                   size_t n, int kbits, uint32_t* d_out, pc2_stream_t stream) {
+  if (!ctx || !key || kbits < 0 || kbits > 32 || n > (size_t)1 << 24 ||
+      (n && (!d_alpha || !d_s || !d_K || !d_out)))
+    return PC2_EINVAL;
+  if (!n) return PC2_OK;
+  const int kb = kbits ? kbits : 32;
+  const cudaStream_t st = (cudaStream_t)stream;
+  switch (2 * key->Lh) {
+    case 16: return block_matvec_any<16>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    case 32: return block_matvec_any<32>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    case 64: return block_matvec_any<64>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    case 128: return block_matvec_any<128>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    case 192: return block_matvec_any<192>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    default: return PC2_EUNSUPPORTED;
+  }
+}
+
+int pc2_admm_save(pc2_admm* A, double* h_x, double* h_z, double* h_v, uint32_t* h_round) {
+  if (!A || !h_x || !h_z || !h_v || !h_round) return PC2_EINVAL;
+  const size_t b = (size_t)A->N * 8;
+  if (cudaMemcpy(h_x, A->x.p, b, cudaMemcpyDeviceToHost) || cudaMemcpy(h_z, A->z.p, b, cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(h_v, A->v.p, b, cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(h_round, A->round_ctr.p, 4, cudaMemcpyDeviceToHost))
+    return PC2_ECUDA;
+  return PC2_OK;
+}
+
+int pc2_admm_load(pc2_admm* A, const double* h_x, const double* h_z, const double* h_v, uint32_t round) {
+  if (!A || !h_x || !h_z || !h_v || round < 1) return PC2_EINVAL;
+  const size_t b = (size_t)A->N * 8;
+  if (cudaDeviceSynchronize() || cudaMemcpy(A->x.p, h_x, b, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(A->z.p, h_z, b, cudaMemcpyHostToDevice) || cudaMemcpy(A->v.p, h_v, b, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(A->round_ctr.p, &round, 4, cudaMemcpyHostToDevice))
+    return PC2_ECUDA;
   return PC2_OK;
 }
 

@@ -116,6 +116,36 @@ __global__ void k_dis_xupdate(const double* __restrict__ alpha, const double* __
   }
 }
 
+// ------------------------------------------------------------------ inverse quantization
+// u = q * (1/S or 1/S^2) + zmin in IEEE double (exact for the quantizer's outputs).
+__global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zmin, double inv_scale,
+                             double* __restrict__ u) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    u[i] = __dadd_rn(__dmul_rn((double)q[i], inv_scale), zmin);
+}
+
+// The exact decode of Theorem 1 for one matvec row per thread (no z/v update):
+// X = D + mS S + 2 mS brow + mS asum + 2 mS^2 nk, x = fl(X) / S^2.
+__global__ void k_decode_matvec(const uint32_t* __restrict__ D, int Lh, size_t n, const long long* __restrict__ brow,
+                                const unsigned long long* __restrict__ asum, const int* __restrict__ nk,
+                                long long mS, long long S, double inv_s2, double* __restrict__ x, int* status) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t hi = 0;
+    for (int j = 4; j < Lh; ++j) hi |= D[tiled_index(i, j, Lh)];
+    const unsigned __int128 d = (unsigned __int128)D[tiled_index(i, 0, Lh)] |
+                                ((unsigned __int128)D[tiled_index(i, 1, Lh)] << 32) |
+                                ((unsigned __int128)D[tiled_index(i, 2, Lh)] << 64) |
+                                ((unsigned __int128)D[tiled_index(i, 3, Lh)] << 96);
+    __int128 X = (__int128)d;
+    X += (__int128)mS * S;
+    X += (__int128)2 * mS * brow[i];
+    X += (__int128)mS * (__int128)asum[i];
+    X += (__int128)2 * mS * mS * nk[i];
+    if (hi || X > (__int128)0x7fffffffffffffffLL || X < -(__int128)0x7fffffffffffffffLL) atomicOr(status, PC2_ST_RANGE);
+    x[i] = __dmul_rn(__ll2double_rn((long long)X), inv_s2);
+  }
+}
+
 // ------------------------------------------------------------------ set-up helpers
 // b_ij as 32-bit digits (Gamma2 values are at most Delta < 2^32).
 __global__ void k_narrow(const uint64_t* __restrict__ q, size_t n, uint32_t* __restrict__ out, int* status) {
@@ -147,6 +177,20 @@ static int grid_for(int n, int threads, int sms) {
   int g = (n + threads - 1) / threads;
   if (g > sms * 8) g = sms * 8;
   return g < 1 ? 1 : g;
+}
+
+int launch_dequantize(const uint64_t* q, size_t n, double zmin, double inv_scale, double* u, int sms, cudaStream_t st) {
+  const int g = grid_for((int)(n < (size_t)1 << 30 ? n : (size_t)1 << 30), 256, sms);
+  k_dequantize<<<g, 256, 0, st>>>(q, n, zmin, inv_scale, u);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
+int launch_decode_matvec(const uint32_t* D, int Lh, size_t n, const long long* brow, const unsigned long long* asum,
+                         const int* nk, long long mS, long long S, double inv_s2, double* x, int* status, int sms,
+                         cudaStream_t st) {
+  const int g = grid_for((int)(n < (size_t)1 << 30 ? n : (size_t)1 << 30), 256, sms);
+  k_decode_matvec<<<g, 256, 0, st>>>(D, Lh, n, brow, asum, nk, mS, S, inv_s2, x, status);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
 int launch_quantize(const double* u, size_t n, double zmin, double scale, double qmax, int negate, uint64_t* q,

@@ -11,6 +11,10 @@ namespace pc2 {
 
 int launch_quantize(const double* u, size_t n, double zmin, double scale, double qmax, int negate, uint64_t* q,
                     int* status, uint32_t* bitlen_or, int sms, cudaStream_t st);
+int launch_dequantize(const uint64_t* q, size_t n, double zmin, double inv_scale, double* u, int sms, cudaStream_t st);
+int launch_decode_matvec(const uint32_t* D, int Lh, size_t n, const long long* brow, const unsigned long long* asum,
+                         const int* nk, long long mS, long long S, double inv_s2, double* x, int* status, int sms,
+                         cudaStream_t st);
 int launch_admm_quant(const double* z, const double* v, int N, const int* node_of, double zmin, double scale,
                       double qmax, uint64_t* zq, uint64_t* vq, unsigned long long* asum, int* status, int sms,
                       cudaStream_t st);

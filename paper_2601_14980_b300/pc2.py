@@ -365,6 +365,17 @@ class Admm:
         _check(_admm_buffers(self.h, *[ctypes.byref(p) for p in ps], ctypes.byref(n)), "pc2_admm_buffers")
         return dict(zip(["zhat", "vhat", "xhat", "alpha_hat", "D"], [p.value for p in ps]), N=n.value)
 
+    def save(self):
+        """Host checkpoint: (x, z, v) as numpy arrays and the next round."""
+        x, z, v = (np.empty(self.N, dtype=np.float64) for _ in range(3))
+        r = _u32()
+        _check(_admm_save(self.h, x.ctypes.data, z.ctypes.data, v.ctypes.data, ctypes.byref(r)), "pc2_admm_save")
+        return x, z, v, r.value
+
+    def load(self, x, z, v, round_: int):
+        x, z, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, z, v))
+        _check(_admm_load(self.h, x.ctypes.data, z.ctypes.data, v.ctypes.data, round_), "pc2_admm_load")
+
     def set_matvec(self, mode: int):
         """0 automatic, 1 one CTA per row tile, 2 bucket windows spread over CTAs."""
         _check(_admm_set_matvec(self.h, mode), "pc2_admm_set_matvec")
@@ -585,3 +596,39 @@ class Server:
         _check(_server_stats(self.h, ctypes.byref(c), ctypes.byref(s), ctypes.byref(i), ctypes.byref(a)),
                "pc2_server_stats")
         return {"completed": c.value, "steps": s.value, "items": i.value, "arena_peak": a.value}
+
+
+_dequantize = _sig("pc2_dequantize", [_vp, _vp, _sz, ctypes.c_double, _i, _i, _vp, _vp])
+_decode_matvec = _sig("pc2_decode_matvec", [_vp, _vp, _i, _sz, _vp, _vp, _vp, ctypes.c_double, _i, _vp, _vp])
+_hom_matvec = _sig("pc2_hom_matvec", [_vp, _vp, _vp, _vp, _vp, _sz, _i, _vp, _vp])
+_admm_save = _sig("pc2_admm_save", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32)])
+_admm_load = _sig("pc2_admm_load", [_vp, _vp, _vp, _vp, _u32])
+
+
+def dequantize(ctx: Context, q, zmin: float, log2_scale: int, gamma: int = 2, out=None, stream=None):
+    """Inverse of quantize: q (int64 tensor of uint64) -> float64 tensor."""
+    import torch
+
+    n = int(q.numel())
+    out = torch.empty(n, dtype=torch.float64, device=q.device) if out is None else out
+    _check(_dequantize(ctx.h, _ptr(q), n, zmin, log2_scale, gamma, _ptr(out), _stream(stream)), "pc2_dequantize")
+    return out
+
+
+def decode_matvec(ctx: Context, D, limbs: int, n: int, brow, asum, nk, zmin: float, log2_scale: int, out=None,
+                  stream=None):
+    """Theorem 1's exact decode of decrypted matvec rows (D tiled, brow int64, asum uint64 as int64, nk int32)."""
+    import torch
+
+    out = torch.empty(n, dtype=torch.float64, device=D.device) if out is None else out
+    _check(_decode_matvec(ctx.h, _ptr(D), limbs, n, _ptr(brow), _ptr(asum), _ptr(nk), zmin, log2_scale, _ptr(out),
+                          _stream(stream)), "pc2_decode_matvec")
+    return out
+
+
+def hom_matvec(ctx: Context, key: Key, alpha, s, K, n: int, kbits: int = 0, out=None, stream=None):
+    """Eq. (itq2) on one n x n block (K: int32 tensor of uint32, row-major)."""
+    out = empty_tiled(n, 2 * key.limbs, s.device) if out is None else out
+    _check(_hom_matvec(ctx.h, key.h, _ptr(alpha), _ptr(s), _ptr(K), n, kbits, _ptr(out), _stream(stream)),
+           "pc2_hom_matvec")
+    return out

@@ -1,0 +1,108 @@
+"""GPU tests of the standalone block operations of the C ABI against the
+oracle: inverse quantization, Theorem 1's exact decode of matvec rows, the
+encrypted matvec of Eq. (itq2) on one block, and the host checkpoint of the
+ADMM object."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import admm as O
+from oracle import paillier as P
+from paper_2601_14980_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+QP = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    return torch, pc2, pc2.Context(0)
+
+
+def test_dequantize_inverts_both_quantizers_exactly(env):
+    torch, pc2, ctx = env
+    rng = np.random.default_rng(1)
+    u = np.concatenate([rng.uniform(-8, 8, 997), [-8.0, 8.0, 0.0]])
+    du = torch.from_numpy(u).cuda()
+    for gamma, oq in ((2, O.gamma2), (1, O.gamma1)):
+        q = pc2.quantize(ctx, du, QP.zmin, QP.zmax, QP.log2_scale, gamma)
+        back = pc2.dequantize(ctx, q, QP.zmin, QP.log2_scale, gamma).cpu().numpy()
+        ref = oq(u, QP)
+        assert np.array_equal(q.cpu().numpy(), ref)
+        s = 2 ** (QP.log2_scale * (2 if gamma == 1 else 1))
+        want = np.array([float(Fraction(int(x), s) + Fraction(QP.zmin)) for x in ref])
+        assert np.array_equal(back, want)
+        assert np.max(np.abs(back - u)) <= 0.5 / s + 1e-15
+    assert ctx.status() == 0
+
+
+def test_decode_matvec_equals_oracle_decode(env):
+    torch, pc2, ctx = env
+    rng = np.random.default_rng(2)
+    n, limbs = 70, 8
+    # magnitudes where the exact sum stays inside 64 bits, as decrypted rows do
+    D = [int(x) for x in rng.integers(0, 1 << 60, n)]
+    brow = rng.integers(0, 1 << 30, n)
+    asum = rng.integers(0, 1 << 33, n).astype(np.uint64)
+    nk = rng.integers(1, 8, n).astype(np.int32)
+    want = np.array([O.decode([D[i]], [int(brow[i])], int(asum[i]), int(nk[i]), QP)[0] for i in range(n)])
+    dD = pc2.ints_to_tiled(ctx, D, limbs)
+    x = pc2.decode_matvec(ctx, dD, limbs, n, torch.from_numpy(brow).cuda(), torch.from_numpy(asum.view(np.int64)).cuda(),
+                          torch.from_numpy(nk).cuda(), QP.zmin, QP.log2_scale)
+    assert np.array_equal(x.cpu().numpy(), want)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("nbits,n,kbits", [(512, 37, 12), (1024, 70, 28), (2048, 20, 5)])
+def test_hom_matvec_block_equals_oracle(env, nbits, n, kbits):
+    torch, pc2, ctx = env
+    p, q = W.primes(nbits, 4)
+    kg, ko = pc2.Key.from_primes(p, q), P.derive_key(p, q)
+    rng = np.random.default_rng(nbits + n)
+    a = W.plaintexts_u64(n, seed=3)
+    s = W.plaintexts_u64(n, seed=4)
+    ah = pc2.encrypt(ctx, kg, torch.from_numpy(a.view(np.int64)).cuda(), 9, 1)
+    sh = pc2.encrypt(ctx, kg, torch.from_numpy(s.view(np.int64)).cuda(), 9, 2)
+    K = rng.integers(0, 1 << kbits, size=(n, n), dtype=np.uint64)
+    dK = torch.from_numpy(K.astype(np.uint32).view(np.int32)).cuda()
+    out = pc2.hom_matvec(ctx, kg, ah, sh, dK, n, kbits)
+    L2 = 2 * kg.limbs
+    got = pc2.tiled_to_ints(ctx, out, n, L2)
+    want = P.hom_matvec(ko, pc2.tiled_to_ints(ctx, ah, n, L2), pc2.tiled_to_ints(ctx, sh, n, L2), K)
+    assert got == want
+    # and the plaintext it carries: a_i + sum_j K_ij s_j mod n
+    dec = pc2.tiled_to_ints(ctx, pc2.decrypt(ctx, kg, out, n), n, kg.limbs)
+    for i in (0, n - 1):
+        assert dec[i] == (int(a[i]) + sum(int(K[i, j]) * int(s[j]) for j in range(n))) % ko.n
+
+
+def test_admm_host_checkpoint_round_trip(env):
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=7, M=30, N=48, nnz=4, K=2)
+    st = O.dis_setup(L.A, L.y, W.node_sizes(48, 2), L.rho)
+    p, q = W.primes(512, 5)
+    kg = pc2.Key.from_primes(p, q)
+    alpha = torch.from_numpy(np.concatenate(st.alpha)).cuda()
+    Bbar = torch.from_numpy(np.concatenate([b.ravel() for b in st.Bbar])).cuda()
+
+    def make():
+        return pc2.Admm(ctx, kg, st.sizes, alpha, Bbar, L.lam, L.rho, QP.zmin, QP.zmax, QP.log2_scale, 13)
+
+    a = make()
+    a.round(2)
+    x, z, v, r = a.save()
+    assert r == 3
+    a.round(2)
+    b = make()
+    b.load(x, z, v, r)
+    b.round(2)
+    for u, w in zip(a.get()[:3], b.get()[:3]):
+        assert torch.equal(u, w)
+    ref = O.quantized_admm(st, L.lam, L.rho, 4, QP)
+    assert np.array_equal(b.get()[2].cpu().numpy(), ref.v[3])
