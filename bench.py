@@ -374,9 +374,9 @@ def run_gpu(args):
     from paper_2601_14980_b300 import pc2
     from paper_2601_14980_b300 import workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2601_14980_b300.dist import max_over_ranks, rank_world, shard
+
+    rank, world, local = rank_world()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -407,7 +407,7 @@ def run_gpu(args):
     dec_host = torch.empty(dec.numel(), dtype=torch.int32).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
     st = torch.cuda.current_stream()
-    e0 = rank * N_PLAIN
+    e0, _ = shard(world * N_PLAIN, rank, world)   # this rank's elements are global indices e0 ..
 
     def step(ev=None, e2e=False):
         if e2e:
@@ -456,10 +456,7 @@ def run_gpu(args):
         e2e_ms.append(a.elapsed_time(b))
     ms_e2e = statistics.mean(e2e_ms)
 
-    if dist:
-        t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
     ops = (N_PLAIN + per_group) * world
     value = ops / (ms / 1e3)
 
