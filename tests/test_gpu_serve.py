@@ -180,3 +180,33 @@ def test_aggregate_from_a_strided_pool(env):
     srv.wait(srv.submit(pc2.OP_AGGREGATE, h_in, count, h_out, groups=3, h_stride=stride))
     srv.close()
     assert torch.equal(pc2.unpack(ctx, h_out.cuda(), count, L2).cpu(), want)
+
+
+def test_concurrent_submitters(env):
+    """Four host threads submit and wait at the same time; every result equals the entry point's."""
+    import threading
+
+    torch, pc2, ctx = env
+    kg, _ = _keys(pc2, 512)
+    rng = np.random.default_rng(3)
+    reqs = _mix(env, kg, 16, rng, lo=20, hi=1500)
+    srv = pc2.Server(ctx, kg, arena_bytes=64 << 20)
+    errors = []
+
+    def worker(chunk):
+        try:
+            ts = [r.submit(srv) for r in chunk]
+            for t in ts:
+                srv.wait(t)
+        except Exception as e:  # noqa: BLE001 - reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(reqs[i::4],)) for i in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=300)
+    assert not errors
+    assert all(r.ok() for r in reqs)
+    assert srv.stats()["completed"] == len(reqs)
+    srv.close()
