@@ -305,7 +305,7 @@ int pc2_batch_ciphertexts(pc2_batch* batch, int which, int node, const uint32_t*
 /* Elements, work items, persistent grid and scratch bytes of the batched launch. */
 int pc2_batch_info(const pc2_batch* batch, size_t* elements, int* items, int* grid, size_t* scratch_bytes);
 /* Autotuner: times the window width (4..6) of each key's exponent schedules
- * and the CTAs per SM (1..2) of the persistent launch on a sample of the work
+ * and the CTAs per SM (1..3) of the persistent launch on a sample of the work
  * list (sample_items; 0 = one wave) without changing the state, and keeps the
  * fastest.  h_result (optional, 6 ints): the window per key size (256, 512,
  * 1024, 2048, 3072 bits; 0 = absent) and the CTAs per SM.  Synchronises. */

@@ -413,7 +413,7 @@ int pc2_batch_tune(pc2_batch* B, int sample_items, pc2_stream_t stream, int* h_r
   const cudaStream_t st = (cudaStream_t)stream;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PC2_ECUDA;
   // the sample: the first items of each class (in work-list order), at most sample_items in all
-  const int per_sm_max = 2;  // the kernel's launch bound
+  const int per_sm_max = 3;
   std::vector<BatchItem> sample;
   {
     int counts[kBatchClasses] = {};

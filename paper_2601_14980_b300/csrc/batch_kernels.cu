@@ -18,8 +18,7 @@
 //                   per-operation kernels).
 //
 // The modular exponentiations run on the register Montgomery core (mont.cuh)
-// with the CRT moduli of one-lane classes in constant memory (two CTAs per SM:
-// the register budget of the 3072-bit class at two lanes per element); the few
+// with the CRT moduli of one-lane classes in constant memory; the few
 // products mod n^2 per element (aggregation, the 28-bit scaling exponent,
 // the product with alpha-hat) run on the word-serial glue.
 #include <cuda_runtime.h>
@@ -150,7 +149,7 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_batch_round(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(kThreads, 3) k_batch_round(const __grid_constant__ BatchParams P) {
   extern __shared__ uint32_t bsh_all[];
   __shared__ uint32_t s_item;
   const uint32_t round = *(volatile const uint32_t*)&P.ctl->round;

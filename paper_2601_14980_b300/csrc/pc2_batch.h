@@ -21,10 +21,10 @@ namespace pc2 {
 constexpr int kBatchClasses = 5;  // key sizes 256, 512, 1024, 2048, 3072 bits (Lh = 8, 16, 32, 64, 96)
 constexpr int kBatchLh[kBatchClasses] = {8, 16, 32, 64, 96};
 // Lanes per element in the batched kernel: one lane up to 2048-bit keys (the
-// CRT moduli are read from constant memory with compile-time offsets), two
-// at 3072 bits (48 limbs per lane with the modulus segment in registers,
-// which needs the register budget of two CTAs per SM).
-constexpr int batch_lanes(int Lh) { return Lh == 96 ? 2 : 1; }
+// CRT moduli are read from constant memory with compile-time offsets), four
+// at 3072 bits (24 limbs per lane with the modulus segment in registers), so
+// that every class fits the kernel's register budget of three CTAs per SM.
+constexpr int batch_lanes(int Lh) { return Lh == 96 ? 4 : 1; }
 constexpr int batch_class(int Lh) {
   return Lh == 8 ? 0 : Lh == 16 ? 1 : Lh == 32 ? 2 : Lh == 64 ? 3 : Lh == 96 ? 4 : -1;
 }
