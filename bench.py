@@ -33,9 +33,9 @@ SEED, STREAM = 0xB300, 1
 METRIC = "Paillier enc/dec per s @2048-bit"
 UNIT = "Paillier enc+dec ops/s"
 # DRAM bytes (read + write) per element of k_enc_crt<64,1> from one ncu capture
-# of this build (2^17 elements: 15.00 GB + 2.83 GB; profiles/k_enc_crt_2048_small_full.md),
-# scaled to a launch by the elements it processes; None once the kernel changes.
-ENC_DRAM_BYTES_PER_ELEM = 136077
+# of this build (profiles/k_enc_crt_2048_small_full.md), scaled to a launch by
+# the elements it processes; None once the kernel changes.
+ENC_DRAM_BYTES_PER_ELEM = None
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
 IMAD_PER_CLK_SM = 64   # 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
 
@@ -461,15 +461,15 @@ def run_gpu(args):
     value = ops / (ms / 1e3)
 
     # roofline of the dominant kernel (encryption): algorithmic IMADs / time
-    mm, lb = key.cost(ctx, pc2.COST_ENCRYPT)
-    imad_per_elem = mm * (4 * lb * lb + lb)
+    mm, mmh, lb = key.cost(ctx, pc2.COST_ENCRYPT)
+    imad_per_elem = key.imads(ctx, pc2.COST_ENCRYPT)
     enc_ms = statistics.mean(t_enc)
     achieved = imad_per_elem * N_PLAIN / (enc_ms / 1e3) / 1e12
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12
-    dmm, dlb = key.cost(ctx, pc2.COST_DECRYPT)
+    dmm, _, dlb = key.cost(ctx, pc2.COST_DECRYPT)
     dec_ms = statistics.mean(t_dec)
     if rank != 0:
         if dist: dist.destroy_process_group()
@@ -483,7 +483,8 @@ def run_gpu(args):
                    "parallelism": "dp%d (independent shards)" % world},
         "detail": {"encrypt_ms": enc_ms, "hom_sum_ms": statistics.mean(t_sum), "decrypt_ms": dec_ms,
                    "enc_per_s": N_PLAIN / (enc_ms / 1e3), "dec_per_s": per_group / (dec_ms / 1e3),
-                   "enc_montmuls_per_elem": mm, "dec_montmuls_per_elem": dmm, "montmul_limbs": lb},
+                   "enc_montmuls_per_elem": mm, "enc_half_width_montmuls_per_elem": mmh,
+                   "dec_montmuls_per_elem": dmm, "montmul_limbs": lb, "enc_imads_per_elem": imad_per_elem},
         "roofline": {"bound": "alu", "kernel": "k_enc_crt", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
                      "frac": achieved / peak, "traffic": ENC_DRAM_BYTES_PER_ELEM * N_PLAIN if ENC_DRAM_BYTES_PER_ELEM else None,
                      "peak_note": "%d SMs x %d IMAD/clk x %.0f MHz (unit count x max SM clock)" % (sms, IMAD_PER_CLK_SM, sm_max)},

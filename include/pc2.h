@@ -110,9 +110,12 @@ int pc2_key_info(const pc2_key* key, int* nbits, int* has_private);
  * words each), lambda and mu (nbits/32 words each).  Any pointer may be NULL. */
 int pc2_key_export(const pc2_key* key, uint32_t* h_n, uint32_t* h_p, uint32_t* h_q, uint32_t* h_lambda, uint32_t* h_mu);
 /* Montgomery products one call costs per element (for throughput accounting):
- * op 0 = pc2_encrypt (key owner, CRT), 1 = public encryption, 2 = decryption;
- * *limbs receives the operand width of those products. */
-int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, int* limbs);
+ * op 0 = pc2_encrypt (key owner, CRT), 1 = public encryption, 2 = decryption.
+ * *montmuls receives the products of *limbs words, *montmuls_half those of
+ * *limbs / 2 words (the half-width powers mod p and q of the key-owner
+ * encryption as the one-lane kernels run it; 0 for ops 1 and 2).  The few
+ * conversion products per element outside the powers are not counted. */
+int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, long* montmuls_half, int* limbs);
 
 /* ---- layout ----------------------------------------------------------- */
 size_t pc2_tiled_words(size_t count, int limbs);

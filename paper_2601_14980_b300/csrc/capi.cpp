@@ -578,8 +578,9 @@ int pc2_key_export(const pc2_key* key, uint32_t* h_n, uint32_t* h_p, uint32_t* h
   return PC2_OK;
 }
 
-int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, int* limbs) {
-  if (!ctx || !key || !montmuls || !limbs) return PC2_EINVAL;
+int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls, long* montmuls_half, int* limbs) {
+  if (!ctx || !key || !montmuls || !montmuls_half || !limbs) return PC2_EINVAL;
+  *montmuls_half = 0;
   const int w = ctx->window;
   int rc = PC2_OK;
   auto fill = [&](auto tag) -> int {
@@ -587,7 +588,12 @@ int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls,
     if (op == 0) {
       auto P = cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, w, [&](EncCrtParams<Lh>& p) { return make_enc_crt<Lh>(*key, w, p); }, &rc);
       if (!P) return rc;
-      *montmuls = (long)P->ep.montmuls + P->eq.montmuls;
+      if constexpr (lift_route<Lh, 1>()) {
+        *montmuls = (long)P->lp.e2.montmuls + P->lq.e2.montmuls;
+        *montmuls_half = (long)P->lp.e1.montmuls + P->lq.e1.montmuls;
+      } else {
+        *montmuls = (long)P->ep.montmuls + P->eq.montmuls;
+      }
       *limbs = Lh;
     } else if (op == 1) {
       auto P = cached<EncPubParams<2 * Lh>>(key, KIND_ENC_PUB, w, [&](EncPubParams<2 * Lh>& p) { return make_enc_pub<2 * Lh>(*key, w, p); }, &rc);

@@ -138,6 +138,20 @@ bool build_sched(const Big& E, int w, Sched<MAXS>& out) {
   return any;
 }
 
+// As build_sched, with the automatic width limited to `cap` (the window table
+// of a launch is sized for one width).
+template <int MAXS>
+static bool build_sched_capped(const Big& E, int w, int cap, Sched<MAXS>& out) {
+  if (w) return sched_for(E, w, out);
+  bool any = false;
+  Sched<MAXS> tmp;
+  for (int ww = 3; ww <= cap; ++ww) {
+    if (!sched_for(E, ww, tmp)) continue;
+    if (!any || tmp.montmuls < out.montmuls) { out = tmp; any = true; }
+  }
+  return any;
+}
+
 template <int L>
 void fill_mod(ModConst<L>& m, const Big& N) {
   std::memset(&m, 0, sizeof(m));
@@ -201,6 +215,16 @@ int make_enc_crt(const pc2_key& k, int w, EncCrtParams<Lh>& P) {
   fill_mod(P.mq, q2);
   const Big ep = mod(k.n, mul(k.p, sub(k.p, one))), eq = mod(k.n, mul(k.q, sub(k.q, one)));
   if (!build_sched(ep, w, P.ep) || !build_sched(eq, w, P.eq)) return PC2_EUNSUPPORTED;
+  // lifted route: s = r^(h' mod (h-1)) mod h, then s^h mod h^2
+  const int cap = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
+  auto lift = [&](LiftConst<Lh>& C, const Big& h, const Big& ho, const Big& h2) {
+    fill_mod(C.h, h);
+    if (!build_sched_capped(mod(ho, sub(h, one)), w, cap, C.e1)) return false;
+    if (!build_sched_capped(h, w, cap, C.e2)) return false;
+    mod(shl(one, 3 * 16 * Lh), h2).to_words(C.lift, Lh);  // R_h^3, R_h = 2^(16 Lh)
+    return true;
+  };
+  if (!lift(P.lp, k.p, k.q, p2) || !lift(P.lq, k.q, k.p, q2)) return PC2_EUNSUPPORTED;
   k.n.to_words(P.nwords, Lh);
   p2.to_words(P.p2, Lh);
   // (p^2)^-1 mod q^2 = (p^-1 mod q^2)^2, p^-1 mod q^2 = p^(q(q-1) - 1)

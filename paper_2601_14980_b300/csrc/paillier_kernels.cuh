@@ -1,9 +1,11 @@
-// paillier_kernels.cu -- the Paillier kernels of libpc2 and their launchers.
+// paillier_kernels.cuh -- the Paillier kernels of libpc2 and their launchers.
 //
 //   k_enc_crt  key-owner encryption, Eq. (itq1) evaluated through the CRT
-//              split of Sec. IV-A: r^n mod p^2 and mod q^2 with the exponent
-//              reduced mod phi(p^2), phi(q^2) (Lemma 1), each half times
-//              g^m = 1 + m n, recombined by Eq. (gA-C-B) (Lemma 2).
+//              split of Sec. IV-A: r^n mod p^2 and mod q^2 (by the lifted
+//              route of LiftConst, or with the exponent reduced mod phi(p^2),
+//              phi(q^2) as in Lemma 1 when a lane would hold fewer than two
+//              half-width limbs), each half times g^m = 1 + m n, recombined
+//              by Eq. (gA-C-B) (Lemma 2).
 //   k_enc_pub  public-key encryption, Eq. (itq1) directly mod n^2.
 //   k_dec_crt  decryption of Sec. III-C via the CRT: m_p = L_p(c^(p-1) mod p^2) h_p
 //              mod p, m_q likewise, Garner recombination mod n (equal to
@@ -111,18 +113,58 @@ struct Layout {
 };
 
 // ------------------------------------------------------------------ CRT encryption
+// A = (r^n mod h^2) R by the lifted route (LiftConst): r mod h from the raw
+// draw X (words [0, Lh + 2)), s = r^(h' mod (h-1)) mod h at half width, then
+// s^h mod h^2.  Uses columns A, B, C, TT; X is read only.
 template <int Lh, int T>
-__device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMaxSched>& E, const Col& X, const Col& GM,
-                                         const Col& OUT, const Col& A, const Col& B, const Col& C, const Col& TT,
-                                         const Col& tab, const Col& bsh, const Grp<T>& g) {
-  constexpr int S = Lh / T;
-  g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // r~ = r R mod h^2
+__device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const LiftConst<Lh>& H, const Col& X, const Col& A,
+                                          const Col& B, const Col& C, const Col& TT, const Col& tab, const Col& bsh,
+                                          const Grp<T>& g) {
+  constexpr int Lp = Lh / 2, Sa = Lp / T, S = Lh / T;
+  // r = x0 + x1 R_h with x0 = words [0, Lp), x1 = words [Lp, 3 Lp) < R_h^2:
+  // r R_h = x0 R_h + (x1 R_h) R_h mod h
+  g_to_mont_2l(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, Lp, B, C, TT);  // x1 R_h
+  g_copy_param(B, H.h.r2, Lp);
+  g_mont(A, A, B, H.h.n, H.h.np, Lp, TT);                                  // x1 R_h^2
+  g_mont(C, X, B, H.h.n, H.h.np, Lp, TT);                                  // x0 R_h
+  g_addmod(A, A, C, H.h.n, Lp);                                            // r R_h mod h
+  __syncwarp();
+  {
+    uint32_t a[Sa];
+    load_seg(a, A, g);
+    run_modexp<Sa, T>(a, H.e1, H.h.n, H.h.np, tab, bsh, g);                // s R_h
+    store_seg(A, a, g);
+  }
+  __syncwarp();
+  for (int j = Lp; j < Lh; ++j) A[j] = 0u;
+  g_copy_param(B, H.lift, Lh);
+  g_mont(A, A, B, M.n, M.np, Lh, TT);                                      // s R mod h^2
   __syncwarp();
   uint32_t a[S];
   load_seg(a, A, g);
-  run_modexp<S, T>(a, E, M.n, M.np, tab, bsh, g);          // (r^n mod h^2) R
+  run_modexp<S, T>(a, H.e2, M.n, M.np, tab, bsh, g);                       // s^h R = (r^n mod h^2) R
   store_seg(A, a, g);
   __syncwarp();
+}
+
+template <int Lh, int T>
+__device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMaxSched>& E, const LiftConst<Lh>& H,
+                                         const Col& X, const Col& GM, const Col& OUT, const Col& A, const Col& B,
+                                         const Col& C, const Col& TT, const Col& tab, const Col& bsh,
+                                         const Grp<T>& g) {
+  constexpr int S = Lh / T;
+  if constexpr (lift_route<Lh, T>()) {
+    rn_lifted<Lh, T>(M, H, X, A, B, C, TT, tab, bsh, g);
+  } else {
+    // direct route: the power by n mod h(h-1)
+    g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // r~ = r R mod h^2
+    __syncwarp();
+    uint32_t a[S];
+    load_seg(a, A, g);
+    run_modexp<S, T>(a, E, M.n, M.np, tab, bsh, g);          // (r^n mod h^2) R
+    store_seg(A, a, g);
+    __syncwarp();
+  }
   g_to_mont_2l(B, GM, M.n, M.r2, M.r3, M.np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
   g_mont(C, A, B, M.n, M.np, Lh, TT);                          // c_h R
   g_zero(B, Lh);
@@ -153,8 +195,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const _
     const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | P.kind) : P.stream;
     gen_r(X, P.seed, sid, P.e0 + e, Lh + 2, 2 * Lh);
     make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid, status);
-    enc_half<Lh, T>(P.mp, P.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
-    enc_half<Lh, T>(P.mq, P.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
+    enc_half<Lh, T>(P.mp, P.ep, P.lp, X, GM, CP, A, B, C, TT, tab, bsh, g);
+    enc_half<Lh, T>(P.mq, P.eq, P.lq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2  (c_p < p^2 < q^2)
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
     g_copy_param(B, P.pinv2R, Lh);
@@ -326,8 +368,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const 
     gen_r(X, P.seed, sid, P.e0 + ei, Lh + 2, 2 * Lh);
     make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid && half == 0, status);
     // the half is uniform per warp; each branch reads its constants at fixed offsets
-    if (half) enc_half<Lh, T>(P.mq, P.eq, X, GM, CH, A, B, C, TT, tab, bsh, g);
-    else enc_half<Lh, T>(P.mp, P.ep, X, GM, CH, A, B, C, TT, tab, bsh, g);
+    if (half) enc_half<Lh, T>(P.mq, P.eq, P.lq, X, GM, CH, A, B, C, TT, tab, bsh, g);
+    else enc_half<Lh, T>(P.mp, P.ep, P.lp, X, GM, CH, A, B, C, TT, tab, bsh, g);
     __syncthreads();
     if (half == 0) {
       // Eq. (gA-C-B) with c_q from the partner group (gl + H) of this CTA

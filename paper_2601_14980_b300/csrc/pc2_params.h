@@ -52,13 +52,33 @@ struct EncPubParams {
   int32_t mwords;          // words per plaintext: 2 (uint64 input) or L2/2 (wide, tiled input)
 };
 
+// r^n mod h^2 for one prime h of the key (h = p or q, h' the other one)
+// without the full power by n mod h(h-1).  Since h | n, r^n mod h^2 depends
+// on r mod h only, and r^h mod h^2 is the Teichmuller representative of
+// r mod h (the unique (h-1)-th root of unity mod h^2 congruent to it); so
+// r^n = (r^h)^(h') is the representative of s = r^(h' mod (h-1)) mod h, which
+// is s^h mod h^2.  One power mod h (half width) by an exponent below h and
+// one power mod h^2 by h replace one power mod h^2 by a full-width exponent.
+template <int Lh>
+struct LiftConst {
+  ModConst<Lh / 2> h;          // the prime h, R_h = 2^(16 Lh)
+  Sched<kMaxSchedHalf> e1;     // h' mod (h - 1)
+  Sched<kMaxSchedHalf> e2;     // h
+  uint32_t lift[Lh];           // R_h^3 mod h^2: Montgomery product with s R_h gives s R mod h^2
+};
+
+// The lifted route needs at least two limbs per lane at half width.
+template <int Lh, int T>
+constexpr bool lift_route() { return (Lh / 2) / T >= 2; }
+
 // Key-owner encryption through CRT mod p^2 and q^2 (Lh = limbs of n = limbs of p^2).
 // When round_ptr is set the r-stream id is (*round_ptr << 8) | kind, read on
 // the device (so a captured ADMM round can be replayed round after round).
 template <int Lh>
 struct EncCrtParams {
   ModConst<Lh> mp, mq;       // p^2, q^2
-  Sched<kMaxSched> ep, eq;   // n mod p(p-1), n mod q(q-1)
+  Sched<kMaxSched> ep, eq;   // n mod p(p-1), n mod q(q-1) (direct route)
+  LiftConst<Lh> lp, lq;      // lifted route mod p^2, q^2 (window widths <= max(ep.w, eq.w))
   uint32_t nwords[Lh];       // n
   uint32_t p2[Lh];           // p^2 (for the recombination product)
   uint32_t pinv2R[Lh];       // (p^-2 mod q^2) * R mod q^2
@@ -107,5 +127,9 @@ struct MatvecParams {
   int32_t ntiles;  // row tiles (a tile = one CTA's rows, all of one node)
   int32_t pad_;
 };
+
+// Kernel parameter blocks travel by value: at most 32764 bytes per launch.
+static_assert(sizeof(EncCrtParams<96>) + 256 <= 32764, "encryption parameter block too large");
+static_assert(sizeof(DecParams<96>) + 256 <= 32764, "decryption parameter block too large");
 
 }  // namespace pc2

@@ -48,7 +48,8 @@ _key_public = _sig("pc2_key_public", [_vp, ctypes.POINTER(_vp)])
 _key_destroy = _sig("pc2_key_destroy", [_vp], None)
 _key_info = _sig("pc2_key_info", [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)])
 _key_export = _sig("pc2_key_export", [_vp, _vp, _vp, _vp, _vp, _vp])
-_key_cost = _sig("pc2_key_cost", [_vp, _vp, _i, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(_i)])
+_key_cost = _sig("pc2_key_cost", [_vp, _vp, _i, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                    ctypes.POINTER(_i)])
 _tiled_words = _sig("pc2_tiled_words", [_sz, _i], _sz)
 _pack = _sig("pc2_pack", [_vp, _vp, _sz, _i, _vp, _vp])
 _unpack = _sig("pc2_unpack", [_vp, _vp, _sz, _i, _vp, _vp])
@@ -190,11 +191,20 @@ class Key:
                "pc2_key_export")
         return {"n": _int_of(n), "p": _int_of(p), "q": _int_of(q), "lambda": _int_of(lam), "mu": _int_of(mu)}
 
-    def cost(self, ctx: Context, op: int) -> tuple[int, int]:
-        """(Montgomery products per element, their limb width) of one op."""
-        mm, lb = ctypes.c_long(), _i()
-        _check(_key_cost(ctx.h, self.h, op, ctypes.byref(mm), ctypes.byref(lb)), "pc2_key_cost")
-        return mm.value, lb.value
+    def cost(self, ctx: Context, op: int) -> tuple[int, int, int]:
+        """(Montgomery products per element of `limbs` words, those of limbs/2
+        words, limbs) of one op."""
+        mm, mh, lb = ctypes.c_long(), ctypes.c_long(), _i()
+        _check(_key_cost(ctx.h, self.h, op, ctypes.byref(mm), ctypes.byref(mh), ctypes.byref(lb)), "pc2_key_cost")
+        return mm.value, mh.value, lb.value
+
+    def imads(self, ctx: Context, op: int) -> int:
+        """Algorithmic 32-bit multiply-adds per element of one op's powers: a
+        Montgomery product of L limbs takes 4 L^2 + L (low and high halves of
+        the L^2 limb products of a*b and of m*N, and L quotient words)."""
+        mm, mh, lb = self.cost(ctx, op)
+        h = lb // 2
+        return mm * (4 * lb * lb + lb) + mh * (4 * h * h + h)
 
 
 # ------------------------------------------------------------------ device buffers

@@ -163,3 +163,28 @@ def test_r_raw_congruence_identity():
         rr = P.r_raw(77, 4, e, P.r_words(k.nbits))
         assert P.powmod(rr, k.n, k.n2) == P.powmod(rr % k.n, k.n, k.n2)
         assert pow(rr, k.n, k.p ** 2) == pow(rr % k.n, k.n, k.p ** 2)
+
+
+@pytest.mark.parametrize("nbits", [256, 1024, 2048])
+def test_lifted_route_identity(nbits):
+    # The encryption kernels compute r^n mod h^2 (h = p, q; h' the other
+    # prime) as s^h mod h^2 with s = (r mod h)^(h' mod (h-1)) mod h: since
+    # h | n, r^n mod h^2 depends on r mod h only, and r^h mod h^2 is the
+    # (h-1)-th root of unity mod h^2 congruent to r mod h.  Checked against the
+    # definition on raw draws wider than n, on r = 0 mod h and on r = 1.
+    k = _key(nbits, seed=9)
+    rng = random.Random(nbits)
+    for h, ho in ((k.p, k.q), (k.q, k.p)):
+        h2 = h * h
+        draws = [P.r_raw(31, 2, e, P.r_words(k.nbits)) for e in range(6)] + [h * 5, 1, k.n - 1]
+        draws += [rng.randrange(1, k.n) for _ in range(6)]
+        for rr in draws:
+            s = pow(rr % h, ho % (h - 1), h)
+            lifted = pow(s, h, h2)
+            assert lifted == pow(rr % k.n, k.n, h2)
+            assert pow(lifted, h - 1, h2) == (0 if rr % h == 0 else 1)   # a root of unity of order | h-1
+            assert lifted % h == pow(rr % h, k.n, h)                        # congruent to r^n mod h
+    # the encryption it feeds agrees with the oracle's definition
+    r = P.r_of(k, 12, 3, 7)
+    cp = pow(pow(r % k.p, k.q % (k.p - 1), k.p), k.p, k.p ** 2) * (1 + 5 * k.n) % (k.p ** 2)
+    assert cp == P.encrypt(k, [5], [r])[0] % (k.p ** 2)
