@@ -110,6 +110,13 @@ static int build_key_block(pc2_batch* B, const pc2_key* key, int we, int wd, Bat
     else dst = hm->m64;
     std::memcpy(dst[0], kb->enc.mp.n, sizeof(uint32_t) * Lh);
     std::memcpy(dst[1], kb->enc.mq.n, sizeof(uint32_t) * Lh);
+    uint32_t(*hd)[Lh / 2] = nullptr;
+    if constexpr (Lh == 8) hd = hm->h8;
+    else if constexpr (Lh == 16) hd = hm->h16;
+    else if constexpr (Lh == 32) hd = hm->h32;
+    else hd = hm->h64;
+    std::memcpy(hd[0], kb->enc.lp.h.n, sizeof(uint32_t) * (Lh / 2));
+    std::memcpy(hd[1], kb->enc.lq.h.n, sizeof(uint32_t) * (Lh / 2));
   }
   const int w = std::max(std::max(kb->enc.ep.w, kb->enc.eq.w), std::max(kb->dec.ep.w, kb->dec.eq.w));
   *tabw = std::max((1 << (w - 1)) * Lh, (1 << 4) * 2 * Lh);  // CRT window tables; 16 entries mod n^2 (scaling)

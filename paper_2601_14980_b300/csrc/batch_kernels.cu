@@ -41,6 +41,16 @@ __device__ __forceinline__ const uint32_t* bmod() {
   else return nullptr;
 }
 
+// Prime of CRT half H (0: p, 1: q) of a one-lane class, in constant memory.
+template <int Lh, int H>
+__device__ __forceinline__ const uint32_t* bprime() {
+  if constexpr (Lh == 8) return c_bmods.h8[H];
+  else if constexpr (Lh == 16) return c_bmods.h16[H];
+  else if constexpr (Lh == 32) return c_bmods.h32[H];
+  else if constexpr (Lh == 64) return c_bmods.h64[H];
+  else return nullptr;
+}
+
 template <int Lh, int T>
 __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem& I, uint32_t round, uint32_t* cta,
                                            uint32_t* bsh_all) {
@@ -74,8 +84,10 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
     const uint32_t sid = (round << 8) | (which ? 2u : 1u);
     gen_r(X, P.seed, sid, e, Lh + 2, L2);
     gm_u64(GM, A, which ? qv : qz, K.enc.nwords, Lh, L2);
-    enc_half_f<Lh, T>(K.enc.mp, bmod<Lh, 0>(), K.enc.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
-    enc_half_f<Lh, T>(K.enc.mq, bmod<Lh, 1>(), K.enc.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
+    enc_half_f<Lh, T>(K.enc.mp, bmod<Lh, 0>(), K.enc.ep, K.enc.lp, bprime<Lh, 0>(), X, GM, CP, A, B, C, TT, tab, bsh,
+                      g);
+    enc_half_f<Lh, T>(K.enc.mq, bmod<Lh, 1>(), K.enc.eq, K.enc.lq, bprime<Lh, 1>(), X, GM, CQ, A, B, C, TT, tab, bsh,
+                      g);
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
     g_copy_param(B, K.enc.pinv2R, Lh);

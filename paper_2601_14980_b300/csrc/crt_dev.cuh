@@ -25,24 +25,30 @@ __device__ __forceinline__ void gm_u64(const Col& GM, const Col& M, uint64_t m, 
 }
 
 // One CRT half of an encryption: OUT = r^n (1 + m n) mod h^2 (h^2 = Mg.n).
-// Mg: the half's constants in device memory; nfast: the same modulus in
+// Mg, Hg: the half's constants in device memory; nfast, hfast: h^2 and h in
 // constant memory (read with compile-time offsets by one-lane products; with
-// T > 1 each lane loads its segment of Mg.n into registers instead).
+// T > 1 each lane loads its segment of Mg.n, Hg.h.n into registers instead).
+// r^n mod h^2 takes the lifted route (LiftConst) where a lane holds at least
+// two half-width limbs, else the power by n mod h(h-1) (schedule E).
 template <int Lh, int T>
 __device__ __forceinline__ void enc_half_f(const ModConst<Lh>& Mg, const uint32_t* nfast, const Sched<kMaxSched>& E,
-                                           const Col& X,
+                                           const LiftConst<Lh>& Hg, const uint32_t* hfast, const Col& X,
                                            const Col& GM, const Col& OUT, const Col& A, const Col& B, const Col& C,
                                            const Col& TT, const Col& tab, const Col& bsh, const Grp<T>& g) {
   constexpr int S = Lh / T;
   const uint32_t np = Mg.np;
-  g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // r R mod h^2
-  __syncwarp();
-  uint32_t a[S];
-  load_seg(a, A, g);
-  if constexpr (T == 1) run_modexp<S, T>(a, E, nfast, np, tab, bsh, g);
-  else run_modexp<S, T>(a, E, Mg.n, np, tab, bsh, g);      // (r^n mod h^2) R
-  store_seg(A, a, g);
-  __syncwarp();
+  if constexpr (lift_route<Lh, T>()) {
+    rn_lifted<Lh, T>(Mg, nfast, Hg, hfast, X, A, B, C, TT, tab, bsh, g);  // (r^n mod h^2) R
+  } else {
+    g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // r R mod h^2
+    __syncwarp();
+    uint32_t a[S];
+    load_seg(a, A, g);
+    if constexpr (T == 1) run_modexp<S, T>(a, E, nfast, np, tab, bsh, g);
+    else run_modexp<S, T>(a, E, Mg.n, np, tab, bsh, g);      // (r^n mod h^2) R
+    store_seg(A, a, g);
+    __syncwarp();
+  }
   g_to_mont_2l(B, GM, Mg.n, Mg.r2, Mg.r3, np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
   g_mont(C, A, B, Mg.n, np, Lh, TT);
   g_zero(B, Lh);

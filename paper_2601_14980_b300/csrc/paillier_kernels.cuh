@@ -115,10 +115,14 @@ struct Layout {
 // ------------------------------------------------------------------ CRT encryption
 // A = (r^n mod h^2) R by the lifted route (LiftConst): r mod h from the raw
 // draw X (words [0, Lh + 2)), s = r^(h' mod (h-1)) mod h at half width, then
-// s^h mod h^2.  Uses columns A, B, C, TT; X is read only.
+// s^h mod h^2.  Uses columns A, B, C, TT; X is read only.  nfast, hfast: h^2
+// and h where one-lane products read them (compile-time offsets into the
+// parameter block or constant memory); with T > 1 each lane loads its
+// segment of M.n, H.h.n into registers.
 template <int Lh, int T>
-__device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const LiftConst<Lh>& H, const Col& X, const Col& A,
-                                          const Col& B, const Col& C, const Col& TT, const Col& tab, const Col& bsh,
+__device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const uint32_t* nfast, const LiftConst<Lh>& H,
+                                          const uint32_t* hfast, const Col& X, const Col& A, const Col& B,
+                                          const Col& C, const Col& TT, const Col& tab, const Col& bsh,
                                           const Grp<T>& g) {
   constexpr int Lp = Lh / 2, Sa = Lp / T, S = Lh / T;
   // r = x0 + x1 R_h with x0 = words [0, Lp), x1 = words [Lp, 3 Lp) < R_h^2:
@@ -132,7 +136,7 @@ __device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const LiftConst
   {
     uint32_t a[Sa];
     load_seg(a, A, g);
-    run_modexp<Sa, T>(a, H.e1, H.h.n, H.h.np, tab, bsh, g);                // s R_h
+    run_modexp<Sa, T>(a, H.e1, T == 1 ? hfast : H.h.n, H.h.np, tab, bsh, g);  // s R_h
     store_seg(A, a, g);
   }
   __syncwarp();
@@ -142,7 +146,7 @@ __device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const LiftConst
   __syncwarp();
   uint32_t a[S];
   load_seg(a, A, g);
-  run_modexp<S, T>(a, H.e2, M.n, M.np, tab, bsh, g);                       // s^h R = (r^n mod h^2) R
+  run_modexp<S, T>(a, H.e2, T == 1 ? nfast : M.n, M.np, tab, bsh, g);      // s^h R = (r^n mod h^2) R
   store_seg(A, a, g);
   __syncwarp();
 }
@@ -154,7 +158,7 @@ __device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMax
                                          const Grp<T>& g) {
   constexpr int S = Lh / T;
   if constexpr (lift_route<Lh, T>()) {
-    rn_lifted<Lh, T>(M, H, X, A, B, C, TT, tab, bsh, g);
+    rn_lifted<Lh, T>(M, M.n, H, H.h.n, X, A, B, C, TT, tab, bsh, g);
   } else {
     // direct route: the power by n mod h(h-1)
     g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // r~ = r R mod h^2

@@ -84,13 +84,17 @@ struct BatchParams {
   long long mS, S;
 };
 
-// Moduli (p^2, q^2) of the classes run with one lane per element, copied to
-// constant memory before each launch.
+// Moduli (p^2, q^2) and primes (p, q) of the classes run with one lane per
+// element, copied to constant memory before each launch.
 struct BatchConstMods {
   uint32_t m8[2][8];
   uint32_t m16[2][16];
   uint32_t m32[2][32];
   uint32_t m64[2][64];
+  uint32_t h8[2][4];
+  uint32_t h16[2][8];
+  uint32_t h32[2][16];
+  uint32_t h64[2][32];
 };
 
 int launch_batch_round(const BatchParams& P, const BatchConstMods* d_mods, size_t smem, int grid, cudaStream_t st);

@@ -59,6 +59,8 @@ struct ServeConst {
   uint32_t mp[Lh];      // p^2
   uint32_t mq[Lh];      // q^2
   uint32_t n2[2 * Lh];  // n^2
+  uint32_t hp[Lh / 2];  // p
+  uint32_t hq[Lh / 2];  // q
 };
 
 struct ServeParams {

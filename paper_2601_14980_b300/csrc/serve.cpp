@@ -180,6 +180,8 @@ static int serve_setup(pc2_server* S) {
   std::memcpy(C.mp, K->enc.mp.n, sizeof(C.mp));
   std::memcpy(C.mq, K->enc.mq.n, sizeof(C.mq));
   std::memcpy(C.n2, K->n2.n, sizeof(C.n2));
+  std::memcpy(C.hp, K->enc.lp.h.n, sizeof(C.hp));
+  std::memcpy(C.hq, K->enc.lq.h.n, sizeof(C.hq));
   if (cudaMalloc(&S->d_key, sizeof(ServeKey<Lh>)) != cudaSuccess || cudaMalloc(&S->d_const, sizeof(C)) != cudaSuccess)
     return PC2_ENOMEM;
   if (cudaMemcpy(S->d_key, K.get(), sizeof(ServeKey<Lh>), cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -49,8 +49,8 @@ __device__ __forceinline__ void serve_encrypt(const ServeKey<Lh>& K, const Serve
   const size_t idx = I.first + (valid ? (uint32_t)cc.gl : I.count - 1u);
   gen_r(X, R.seed, R.stream, R.e0 + idx, Lh + 2, L2);
   gm_u64(GM, A, R.m64[idx], K.enc.nwords, Lh, L2);
-  enc_half_f<Lh, T>(K.enc.mp, serve_const<Lh>().mp, K.enc.ep, X, GM, CP, A, B, C, TT, tab, bsh, g);
-  enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
+  enc_half_f<Lh, T>(K.enc.mp, serve_const<Lh>().mp, K.enc.ep, K.enc.lp, serve_const<Lh>().hp, X, GM, CP, A, B, C, TT, tab, bsh, g);
+  enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, K.enc.lq, serve_const<Lh>().hq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
   // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2
   if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
   g_copy_param(B, K.enc.pinv2R, Lh);
@@ -119,8 +119,8 @@ __device__ __forceinline__ void serve_encrypt_split(const ServeKey<Lh>& K, const
   const size_t idx = I.first + (valid ? (uint32_t)pe : I.count - 1u);
   gen_r(X, R.seed, R.stream, R.e0 + idx, Lh + 2, L2);
   gm_u64(GM, A, R.m64[idx], K.enc.nwords, Lh, L2);
-  if (half) enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, X, GM, CH, A, B, C, TT, tab, bsh, g);
-  else enc_half_f<Lh, T>(K.enc.mp, serve_const<Lh>().mp, K.enc.ep, X, GM, CH, A, B, C, TT, tab, bsh, g);
+  if (half) enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, K.enc.lq, serve_const<Lh>().hq, X, GM, CH, A, B, C, TT, tab, bsh, g);
+  else enc_half_f<Lh, T>(K.enc.mp, serve_const<Lh>().mp, K.enc.ep, K.enc.lp, serve_const<Lh>().hp, X, GM, CH, A, B, C, TT, tab, bsh, g);
   __syncthreads();
   if (!half) {
     const Col CP = CH, CQ{CH.p + H, CH.s};
