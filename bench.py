@@ -33,9 +33,9 @@ SEED, STREAM = 0xB300, 1
 METRIC = "Paillier enc/dec per s @2048-bit"
 UNIT = "Paillier enc+dec ops/s"
 # DRAM bytes (read + write) per element of k_enc_crt<64,1> from one ncu capture
-# of this build (profiles/k_enc_crt_2048_small_full.md), scaled to a launch by
-# the elements it processes; None once the kernel changes.
-ENC_DRAM_BYTES_PER_ELEM = None
+# of this build (2^17 elements: 10.77 GB + 4.27 GB; profiles/k_enc_crt_2048_small_full.md),
+# scaled to a launch by the elements it processes; None once the kernel changes.
+ENC_DRAM_BYTES_PER_ELEM = 114776
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
 IMAD_PER_CLK_SM = 64   # 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
 
