@@ -367,6 +367,72 @@ def run_serve(dev, rates=(5.0, 15.0, 30.0, 45.0, 60.0), seconds: float = 4.0, se
             "points": points, "status": ctx.status()}
 
 
+# The paper's Table II, master node GPU (RTX 4060), for context only: ops/s.
+PAPER_TABLE2_RTX4060 = {
+    1024: {"modmult": 4062.66e3, "modexp": 79352.5, "ep": 137807.85},
+    2048: {"modmult": 1544.13e3, "modexp": 31080.16, "ep": 65662.72},
+    4096: {"modmult": 1414.34e3, "modexp": 26594.01, "ep": 50053.47},
+}
+
+
+def run_table2(dev, count: int = 9000, trials: int = 10):
+    """Throughput of the operations of the paper's Table II on B300, on its
+    workload: 9000 plaintexts uniform in [0, n), modulus n^2, mean of 10
+    trials, at n = 1024, 2048 and 4096.  ModMult = one product of two
+    ciphertexts mod n^2 (pc2_hom_add); ModExp = c^k mod n^2 with k uniform in
+    [0, n) (pc2_hom_scal_wide); EP = the key-owner encryption of a plaintext
+    in [0, n) through the CRT halves (pc2_encrypt_wide); also public-key
+    encryption (64-bit plaintexts) and CRT decryption.  Inputs resident in
+    device memory; each trial timed with CUDA events after one warm-up."""
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+    from paper_2601_14980_b300 import workloads as W
+
+    ctx = pc2.Context(dev)
+    st = torch.cuda.current_stream()
+    rows = {}
+    for nbits in (1024, 2048, 4096):
+        key = pc2.Key.generate(nbits, 2026)
+        n = key.export()["n"]
+        L, L2 = key.limbs, 2 * key.limbs
+        m = pc2.ints_to_tiled(ctx, W.uniform_below(n, count, nbits), L)
+        kexp = pc2.ints_to_tiled(ctx, W.uniform_below(n, count, nbits + 1), L)
+        m64 = torch.from_numpy(W.plaintexts_u64(count, seed=nbits).view("int64")).to(dev)
+        ct = pc2.encrypt_wide(ctx, key, m, count, SEED, STREAM)
+        ct2 = pc2.encrypt_wide(ctx, key, m, count, SEED, STREAM + 1)
+        out = pc2.empty_tiled(count, L2)
+        dec = pc2.empty_tiled(count, L)
+        ops = {
+            "modmult": lambda: pc2.hom_add(ctx, key, ct, ct2, count, out=out),
+            "modexp": lambda: pc2.hom_scal_wide(ctx, key, ct, kexp, count, out=out),
+            "ep": lambda: pc2.encrypt_wide(ctx, key, m, count, SEED, STREAM, out=out),
+            "encrypt_public": lambda: pc2.encrypt(ctx, key, m64, SEED, STREAM, out=out, public=True),
+            "decrypt": lambda: pc2.decrypt(ctx, key, ct, count, out=dec),
+        }
+        row = {}
+        for name, fn in ops.items():
+            fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(trials):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                fn()
+                b.record(st)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            row[name] = count / (statistics.mean(ms) / 1e3)
+        assert ctx.status() == 0
+        paper = PAPER_TABLE2_RTX4060[nbits]
+        row["paper_rtx4060"] = paper
+        row["ratio_to_paper"] = {k: row[k] / paper[k] for k in paper}
+        rows[str(nbits)] = row
+        del ct, ct2, out, dec, m, kexp
+    return {"workload": "Table II: %d plaintexts uniform in [0, n), modulus n^2, mean of %d trials" % (count, trials),
+            "unit": "ops/s", "rows": rows}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -496,6 +562,7 @@ def run_gpu(args):
         "admm": None if args.no_admm else run_admm(dev),
         "batch": None if args.no_batch else run_batch(dev, args.batch_rounds),
         "serve": None if args.no_serve else run_serve(dev),
+        "table2": None if args.no_table2 else run_table2(dev),
         "admm_full": run_admm_full(dev) if args.admm_full else None,
     }
     print(json.dumps(line))
@@ -529,6 +596,7 @@ def main():
     ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-table2", action="store_true", help="skip the Table II operations at 1024/2048/4096 bits")
     ap.add_argument("--admm-full", action="store_true", help="also time the full-scale 3072-bit ADMM (about 2 min)")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")

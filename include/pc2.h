@@ -21,8 +21,12 @@
  *    A tiled buffer of `count` elements holds pc2_tiled_words(count, limbs)
  *    words.  pc2_pack / pc2_unpack convert from / to the canonical layout
  *    (element e at words [e*limbs, (e+1)*limbs)).
- *  - Key sizes: n of 256, 512, 1024, 2048 or 3072 bits.  Plaintexts have
- *    nbits/32 limbs, ciphertexts nbits/16 limbs.
+ *  - Key sizes: n of 256, 512, 1024, 2048, 3072 or 4096 bits (the paper's
+ *    evaluation uses 1024, 2048 and 4096).  Plaintexts have nbits/32 limbs,
+ *    ciphertexts nbits/16 limbs.  The encrypted matvec and the ADMM objects
+ *    built on it (pc2_hom_matvec, pc2_admm_*) take keys up to 3072 bits, the
+ *    batched round (pc2_batch_*) the five sizes up to 3072 bits, the server
+ *    512- and 2048-bit keys; other calls return PC2_EUNSUPPORTED.
  *  - Scratch: a context owns device scratch memory and grows it on the first
  *    call that needs more (cudaMalloc; synchronises the device).  Call
  *    pc2_ctx_reserve() first to avoid growth inside timed regions or stream
@@ -157,6 +161,14 @@ int pc2_hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t g
 /* Definition 2 (Eq. (hemul)): d_out[i] = d_ct[i]^k[i] mod n^2 (encrypts k m mod n). */
 int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint64_t* d_k, size_t count,
                  uint32_t* d_out, pc2_stream_t cstream);
+/* Definition 2 with a full-width scalar (k in Z_n, as Definition 2 states it):
+ * d_out[i] = d_ct[i]^k[i] mod n^2, d_k a tiled array of `count` scalars of
+ * nbits/32 limbs each (any k < 2^nbits).  Every element takes the same
+ * number of window steps (fixed windows over all nbits bits; the context's
+ * window width clamped to 4..6, else 5), so a short k costs as much as a long
+ * one.  This is also the plain power mod n^2 by a full-width exponent. */
+int pc2_hom_scal_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint32_t* d_k, size_t count,
+                      uint32_t* d_out, pc2_stream_t cstream);
 
 /* ---- quantizer ------------------------------------------------------- *
  * Eq. (et21) with one public range [zmin, zmax] and scale S = 2^log2_scale

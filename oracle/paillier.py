@@ -203,6 +203,12 @@ def hom_scal(key: Key, c: Sequence[int], k: Sequence[int]) -> list[int]:
     return [_int(out[i * cw:(i + 1) * cw]) for i in range(cnt)]
 
 
+def hom_scal_wide(key: Key, c: Sequence[int], k: Sequence[int]) -> list[int]:
+    """Definition 2 (Eq. (hemul)) with k in Z_n as the definition states it:
+    c^k mod n^2 for full-width k, by the oracle's binary exponentiation."""
+    return [powmod(int(ci), int(ki), key.n2) for ci, ki in zip(c, k)]
+
+
 def hom_matvec(key: Key, alpha: Sequence[int], s: Sequence[int], K: np.ndarray) -> list[int]:
     """Eq. (itq2): out_i = alpha_i (+) sum_j K_ij (x) s_j, i.e.
     alpha_i * prod_j s_j^{K_ij} mod n^2 (Definitions 1 and 2, row by row)."""

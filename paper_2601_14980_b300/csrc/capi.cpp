@@ -57,7 +57,7 @@ static std::shared_ptr<P> cached(const pc2_key* k, int kind, int window, F make,
   return p;
 }
 
-enum { KIND_ENC_CRT = 1, KIND_ENC_PUB = 2, KIND_DEC = 3 };
+enum { KIND_ENC_CRT = 1, KIND_ENC_PUB = 2, KIND_DEC = 3, KIND_HOM = 64 };  // KIND_HOM + operands (1..32)
 
 static uint32_t* ctx_scratch(void* c, size_t bytes) {
   pc2_ctx* ctx = static_cast<pc2_ctx*>(c);
@@ -81,7 +81,7 @@ const int* lane_set(int op, int limbs, int* n) {
     switch (limbs) {
       case 8: *n = 3; return s124;
       case 16: case 32: case 64: *n = 4; return s1248;
-      case 96: *n = 3; return s248;
+      case 96: case 128: *n = 3; return s248;
     }
   }
   *n = 1;
@@ -132,7 +132,8 @@ LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
 
 template <int Lh, int T>
 constexpr bool crt_has() {
-  return (Lh == 8 && T <= 4) || ((Lh == 16 || Lh == 32 || Lh == 64) && T <= 8) || (Lh == 96 && T >= 2 && T <= 8);
+  return (Lh == 8 && T <= 4) || ((Lh == 16 || Lh == 32 || Lh == 64) && T <= 8) ||
+         ((Lh == 96 || Lh == 128) && T >= 2 && T <= 8);
 }
 // Calls fn(std::integral_constant<int, T>) for a built lane count T.
 template <int Lh, class Fn>
@@ -216,6 +217,7 @@ int encrypt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_m, size_t 
     case 32: return PC2_CALL_ROUND(32);
     case 64: return PC2_CALL_ROUND(64);
     case 96: return PC2_CALL_ROUND(96);
+    case 128: return PC2_CALL_ROUND(128);
     default: return PC2_EUNSUPPORTED;
   }
 #undef PC2_CALL_ROUND
@@ -261,6 +263,7 @@ template std::shared_ptr<DecParams<16>> dec_params<16>(const pc2_key*, int*);
 template std::shared_ptr<DecParams<32>> dec_params<32>(const pc2_key*, int*);
 template std::shared_ptr<DecParams<64>> dec_params<64>(const pc2_key*, int*);
 template std::shared_ptr<DecParams<96>> dec_params<96>(const pc2_key*, int*);
+template std::shared_ptr<DecParams<128>> dec_params<128>(const pc2_key*, int*);
 
 template <int L2>
 static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs, size_t groups, size_t count,
@@ -269,14 +272,16 @@ static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs
   size_t done = 0;
   bool first = true;
   while (done < groups) {
-    std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>);
-    if (!P) return PC2_ENOMEM;
     int k = 0;
     const uint32_t* ops[kMaxGroups];
     if (!first) ops[k++] = out;
     while (k < kMaxGroups && done < groups) ops[k++] = srcs[done++];
-    int rc = make_hom<L2>(*key, ctx->window, k, *P);
-    if (rc) return rc;
+    int rc;
+    auto P0 = cached<HomParams<L2>>(key, KIND_HOM + k, 0, [&](HomParams<L2>& p) { return make_hom<L2>(*key, 0, k, p); },
+                                    &rc);
+    if (!P0) return rc;
+    std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>(*P0));
+    if (!P) return PC2_ENOMEM;
     for (int i = 0; i < k; ++i) P->src[i] = ops[i];
     rc = launch_hom_sum<L2, lanes_for(L2)>(*P, count, out, ctx->sms, st, base);
     if (rc) return rc;
@@ -295,6 +300,7 @@ int hom_add_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* a, const uint32
     case 32: return hom_sum<64>(ctx, key, srcs, 2, count, out, st, base);
     case 64: return hom_sum<128>(ctx, key, srcs, 2, count, out, st, base);
     case 96: return hom_sum<192>(ctx, key, srcs, 2, count, out, st, base);
+    case 128: return hom_sum<256>(ctx, key, srcs, 2, count, out, st, base);
     default: return PC2_EUNSUPPORTED;
   }
 }
@@ -309,6 +315,7 @@ int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
     case 32: return dec<32>(ctx, key, ct, count, out, st, base);
     case 64: return dec<64>(ctx, key, ct, count, out, st, base);
     case 96: return dec<96>(ctx, key, ct, count, out, st, base);
+    case 128: return dec<128>(ctx, key, ct, count, out, st, base);
     default: return PC2_EUNSUPPORTED;
   }
 }
@@ -316,11 +323,24 @@ int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
 template <int L2>
 static int hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, const uint64_t* k, size_t count,
                     uint32_t* out, cudaStream_t st) {
-  std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>);
-  if (!P) return PC2_ENOMEM;
-  int rc = make_hom<L2>(*key, ctx->window ? (ctx->window > 5 ? 5 : ctx->window) : 4, 1, *P);
-  if (rc) return rc;
+  const int w = ctx->window ? (ctx->window > 5 ? 5 : ctx->window) : 4;
+  int rc;
+  auto P = cached<HomParams<L2>>(key, KIND_HOM + 1, w, [&](HomParams<L2>& p) { return make_hom<L2>(*key, w, 1, p); },
+                                 &rc);
+  if (!P) return rc;
   return launch_hom_scal<L2, lanes_for(L2)>(*P, ct, k, count, out, ctx_scratch, ctx, ctx->sms, st);
+}
+
+// Window of a full-width scalar: the context's width clamped to 4..6, else 5.
+template <int L2>
+static int hom_scal_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, const uint32_t* kw, size_t count,
+                         uint32_t* out, cudaStream_t st) {
+  const int w = ctx->window ? (ctx->window < 4 ? 4 : (ctx->window > 6 ? 6 : ctx->window)) : 5;
+  int rc;
+  auto P = cached<HomParams<L2>>(key, KIND_HOM + 1, w, [&](HomParams<L2>& p) { return make_hom<L2>(*key, w, 1, p); },
+                                 &rc);
+  if (!P) return rc;
+  return launch_hom_scal_wide<L2, lanes_for(L2)>(*P, ct, kw, count, out, ctx_scratch, ctx, ctx->sms, st);
 }
 
 }  // namespace pc2
@@ -334,6 +354,7 @@ using namespace pc2;
     case 32: return call(32);    \
     case 64: return call(64);    \
     case 96: return call(96);    \
+    case 128: return call(128);  \
     default: return PC2_EUNSUPPORTED; \
   }
 
@@ -616,6 +637,7 @@ int pc2_key_cost(const pc2_ctx* ctx, const pc2_key* key, int op, long* montmuls,
     case 32: return fill(std::integral_constant<int, 32>());
     case 64: return fill(std::integral_constant<int, 64>());
     case 96: return fill(std::integral_constant<int, 96>());
+    case 128: return fill(std::integral_constant<int, 128>());
     default: return PC2_EUNSUPPORTED;
   }
 }
@@ -709,6 +731,16 @@ int pc2_hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const u
   const cudaStream_t st = (cudaStream_t)cstream;
 #define PC2_CALL_SCAL(L) hom_scal<2 * L>(ctx, key, d_ct, d_k, count, d_out, st)
   PC2_DISPATCH_H(key->Lh, PC2_CALL_SCAL)
+}
+
+int pc2_hom_scal_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint32_t* d_k, size_t count,
+                      uint32_t* d_out, pc2_stream_t cstream) {
+  if (!ctx || !key) return PC2_EINVAL;
+  if (!count) return PC2_OK;
+  if (!d_ct || !d_k || !d_out) return PC2_EINVAL;
+  const cudaStream_t st = (cudaStream_t)cstream;
+#define PC2_CALL_SCALW(L) hom_scal_wide<2 * L>(ctx, key, d_ct, d_k, count, d_out, st)
+  PC2_DISPATCH_H(key->Lh, PC2_CALL_SCALW)
 }
 
 }  // extern "C"

@@ -20,7 +20,7 @@
 namespace pc2 {
 
 bool supported_nbits(int nbits) {
-  return nbits == 256 || nbits == 512 || nbits == 1024 || nbits == 2048 || nbits == 3072;
+  return nbits == 256 || nbits == 512 || nbits == 1024 || nbits == 2048 || nbits == 3072 || nbits == 4096;
 }
 
 static const uint32_t kSmallPrimes[] = {
@@ -295,10 +295,12 @@ PC2_KEY_INST_H(16)
 PC2_KEY_INST_H(32)
 PC2_KEY_INST_H(64)
 PC2_KEY_INST_H(96)
+PC2_KEY_INST_H(128)
 PC2_KEY_INST_2(16)
 PC2_KEY_INST_2(32)
 PC2_KEY_INST_2(64)
 PC2_KEY_INST_2(128)
 PC2_KEY_INST_2(192)
+PC2_KEY_INST_2(256)
 
 }  // namespace pc2

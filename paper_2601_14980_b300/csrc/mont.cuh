@@ -281,13 +281,15 @@ __device__ __forceinline__ void modexp_sched(uint32_t (&a)[S], const Sched<MAXS>
   }
 }
 
-// a <- a^k (Montgomery domain) for a per-element exponent k < 2^64 with
-// fixed windows of w bits.  tab: 2^w entries (tab[d] = x^d, tab[0] = R mod N);
-// nd: number of digits (warp-uniform).  Every digit costs w squarings and one
-// multiply, so control flow is the same for every lane.
-template <int S, int T, class NS>
-__device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, int nd, const uint32_t* r1,
-                                           const Col tab, const Col bsh, const NS& n, uint32_t np, const Grp<T>& g) {
+// a <- a^k (Montgomery domain) for a per-element exponent given as nd digits
+// of w bits, most significant first: digit(pos) returns digit pos (pos = nd-1
+// down to 0).  tab: 2^w entries (tab[d] = x^d, tab[0] = R mod N); nd is
+// warp-uniform.  Every digit costs w squarings and one multiply, so control
+// flow is the same for every lane.
+template <int S, int T, class NS, class DigitFn>
+__device__ __forceinline__ void modexp_digits(uint32_t (&a)[S], DigitFn digit, int w, int nd, const uint32_t* r1,
+                                              const Col tab, const Col bsh, const NS& n, uint32_t np,
+                                              const Grp<T>& g) {
   constexpr int L = S * T;
   const int ntab = 1 << w;
   // tab[0] = 1 (Montgomery), tab[1] = x, tab[d] = tab[d-1] * x
@@ -296,11 +298,10 @@ __device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, 
   store_seg(tab.off(L), a, g);
   store_seg(bsh, a, g);
   __syncwarp();
-  const uint32_t mask = (uint32_t)ntab - 1u;
   int phase = (ntab > 2) ? 1 : 2, d = 2, pos = nd - 1, sq = 0;
   if (phase == 2) {
     // no table products needed: start the digit loop directly
-    load_seg(a, tab.off((int)((k >> (pos * w)) & mask) * L), g);
+    load_seg(a, tab.off(digit(pos) * L), g);
     --pos;
     if (pos < 0) return;
     store_seg(bsh, a, g);
@@ -314,7 +315,7 @@ __device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, 
       store_seg(tab.off(d * L), a, g);
       if (++d < ntab) continue;
       phase = 2;
-      load_seg(a, tab.off((int)((k >> (pos * w)) & mask) * L), g);
+      load_seg(a, tab.off(digit(pos) * L), g);
       --pos;
       if (pos < 0) return;
       store_seg(bsh, a, g);
@@ -333,7 +334,7 @@ __device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, 
       ++sq;
       store_seg(bsh, a, g);
       __syncwarp();
-      load_seg(a, tab.off((int)((k >> (pos * w)) & mask) * L), g);
+      load_seg(a, tab.off(digit(pos) * L), g);
       continue;
     }
     // multiply done: next digit
@@ -343,6 +344,15 @@ __device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, 
     store_seg(bsh, a, g);
     __syncwarp();
   }
+}
+
+// a <- a^k (Montgomery domain) for a per-element exponent k < 2^64 with
+// fixed windows of w bits over nd digits (warp-uniform).
+template <int S, int T, class NS>
+__device__ __forceinline__ void modexp_var(uint32_t (&a)[S], uint64_t k, int w, int nd, const uint32_t* r1,
+                                           const Col tab, const Col bsh, const NS& n, uint32_t np, const Grp<T>& g) {
+  const uint64_t mask = ((uint64_t)1 << w) - 1u;
+  modexp_digits<S, T>(a, [&](int pos) { return (int)((k >> (pos * w)) & mask); }, w, nd, r1, tab, bsh, n, np, g);
 }
 
 // ---------------------------------------------------------------- glue (word-serial)

@@ -13,6 +13,7 @@
 //              acceleration applies to c^lambda).
 //   k_hom_sum  Definition 1 over several operands: prod_g c_g mod n^2.
 //   k_hom_scal Definition 2: c^k mod n^2, per-element k < 2^64.
+//   k_hom_scal_wide  Definition 2 with a full-width scalar k < 2^nbits.
 //
 // All modexp kernels are persistent: a grid of (SMs x resident CTAs) walks the
 // elements; each element is owned by a group of T lanes (mont.cuh).  Scratch
@@ -513,6 +514,61 @@ __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_scal(const 
     const int nd = (bits + P.w - 1) / P.w;
     if constexpr (T == 1) modexp_var<S, T>(a, k, P.w, nd, P.m.r1, tab, bsh, ParamN{P.m.n}, P.m.np, g);
     else modexp_var<S, T>(a, k, P.w, nd, P.m.r1, tab, bsh, rn, P.m.np, g);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < S; ++j) bsh[g.k * S + j] = (g.k == 0 && j == 0) ? 1u : 0u;
+    __syncwarp();
+    if constexpr (T == 1) mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+    else mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+    __syncwarp();
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < S; ++j) out[tiled_index(e, g.k * S + j, L2)] = a[j];
+    }
+  }
+}
+
+// Definition 2 with a full-width scalar: c^k mod n^2 for a per-element k of
+// Lk = L2 / 2 words (tiled input).  Fixed windows of P.w bits over all Lk
+// words, the same number of digits for every element.
+template <int L2, int T>
+__global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_hom_scal_wide(const __grid_constant__ HomParams<L2> P,
+                                                       const uint32_t* __restrict__ ct,
+                                                       const uint32_t* __restrict__ kw, size_t count,
+                                                       uint32_t* __restrict__ out, uint32_t* __restrict__ scratch) {
+  constexpr int S = L2 / T, Lk = L2 / 2;
+  extern __shared__ uint32_t bsh_all[];
+  const Grp<T> g;
+  const Layout ly(T);
+  const Col bsh{bsh_all + ly.gl, ly.G};
+  const Col tab = ly.slot(scratch, 0);
+  RegN<S> rn;
+  if constexpr (T > 1) rn = reg_n<S, T>(P.m.n, g);
+  const int w = P.w;
+  const uint32_t mask = (1u << w) - 1u;
+  const int nd = (32 * Lk + w - 1) / w;
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    uint32_t a[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) a[j] = ct[tiled_index(e, g.k * S + j, L2)];
+#pragma unroll
+    for (int j = 0; j < S; ++j) bsh[g.k * S + j] = P.m.r2[g.k * S + j];
+    __syncwarp();
+    if constexpr (T == 1) mont_mul<S, T>(a, bsh.p, bsh.s, ParamN{P.m.n}, P.m.np, g);
+    else mont_mul<S, T>(a, bsh.p, bsh.s, rn, P.m.np, g);
+    __syncwarp();
+    // digit pos: bits [pos w, pos w + w) of k, read across a word boundary when needed
+    auto digit = [&](int pos) {
+      const int b0 = pos * w, wi = b0 >> 5, sh = b0 & 31;
+      uint64_t v = kw[tiled_index(e, wi, Lk)];
+      if (wi + 1 < Lk) v |= (uint64_t)kw[tiled_index(e, wi + 1, Lk)] << 32;
+      return (int)((uint32_t)(v >> sh) & mask);
+    };
+    if constexpr (T == 1) modexp_digits<S, T>(a, digit, w, nd, P.m.r1, tab, bsh, ParamN{P.m.n}, P.m.np, g);
+    else modexp_digits<S, T>(a, digit, w, nd, P.m.r1, tab, bsh, rn, P.m.np, g);
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < S; ++j) bsh[g.k * S + j] = (g.k == 0 && j == 0) ? 1u : 0u;

@@ -104,6 +104,20 @@ int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* 
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
+template <int L2, int T>
+int launch_hom_scal_wide(const HomParams<L2>& P, const uint32_t* ct, const uint32_t* kw, size_t count, uint32_t* out,
+                         ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)L2 * (kThreads / T) * 4;
+  auto kern = k_hom_scal_wide<L2, T>;
+  const int grid = occupancy_grid(kern, smem, sms);
+  if (grid < 0) return PC2_ECUDA;
+  const size_t per_group = (size_t)(1 << P.w) * L2;
+  uint32_t* scratch = scratch_fn(sctx, per_group * (size_t)grid * (kThreads / T) * 4);
+  if (!scratch) return PC2_ENOMEM;
+  kern<<<grid, kThreads, smem, st>>>(P, ct, kw, count, out, scratch);
+  return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
+}
+
 // Split-halves variants (T > 1): same arguments, same results.
 template <int Lh, int T>
 int launch_enc_crt2(const EncCrtParams<Lh>& P, const uint64_t* m64, const uint32_t* mwide, size_t count, uint32_t* out,

@@ -40,6 +40,9 @@ int launch_hom_sum(const HomParams<L2>& P, size_t count, uint32_t* out, int sms,
 template <int L2, int T>
 int launch_hom_scal(const HomParams<L2>& P, const uint32_t* ct, const uint64_t* k, size_t count, uint32_t* out,
                     ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st);
+template <int L2, int T>
+int launch_hom_scal_wide(const HomParams<L2>& P, const uint32_t* ct, const uint32_t* kw, size_t count, uint32_t* out,
+                         ScratchFn scratch_fn, void* sctx, int sms, cudaStream_t st);
 int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st);
 int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st);
 

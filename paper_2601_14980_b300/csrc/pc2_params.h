@@ -129,7 +129,9 @@ struct MatvecParams {
 };
 
 // Kernel parameter blocks travel by value: at most 32764 bytes per launch.
-static_assert(sizeof(EncCrtParams<96>) + 256 <= 32764, "encryption parameter block too large");
-static_assert(sizeof(DecParams<96>) + 256 <= 32764, "decryption parameter block too large");
+static_assert(sizeof(EncCrtParams<128>) + 256 <= 32764, "encryption parameter block too large");
+static_assert(sizeof(DecParams<128>) + 256 <= 32764, "decryption parameter block too large");
+static_assert(sizeof(EncPubParams<256>) + 256 <= 32764, "encryption parameter block too large");
+static_assert(sizeof(HomParams<256>) + 256 <= 32764, "homomorphic parameter block too large");
 
 }  // namespace pc2

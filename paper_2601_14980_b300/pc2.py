@@ -60,6 +60,7 @@ _decrypt = _sig("pc2_decrypt", [_vp, _vp, _vp, _sz, _vp, _vp])
 _hom_add = _sig("pc2_hom_add", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
 _hom_sum = _sig("pc2_hom_sum", [_vp, _vp, _vp, _sz, _sz, _vp, _vp])
 _hom_scal = _sig("pc2_hom_scal", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
+_hom_scal_wide = _sig("pc2_hom_scal_wide", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
 
 ST_RANGE, ST_QUANT, ST_TIMEOUT = 1, 2, 4
 COST_ENCRYPT, COST_ENCRYPT_PUBLIC, COST_DECRYPT = 0, 1, 2  # pc2_key_cost operations
@@ -287,6 +288,13 @@ def hom_sum(ctx: Context, key: Key, ct_groups, groups: int, count: int, out=None
 def hom_scal(ctx: Context, key: Key, ct, k, count: int, out=None, stream=None):
     out = empty_tiled(count, 2 * key.limbs, ct.device) if out is None else out
     _check(_hom_scal(ctx.h, key.h, _ptr(ct), _ptr(k), count, _ptr(out), _stream(stream)), "pc2_hom_scal")
+    return out
+
+
+def hom_scal_wide(ctx: Context, key: Key, ct, k, count: int, out=None, stream=None):
+    """c_i^{k_i} mod n^2 with k a tiled array of full-width scalars (nbits/32 limbs)."""
+    out = empty_tiled(count, 2 * key.limbs, ct.device) if out is None else out
+    _check(_hom_scal_wide(ctx.h, key.h, _ptr(ct), _ptr(k), count, _ptr(out), _stream(stream)), "pc2_hom_scal_wide")
     return out
 
 

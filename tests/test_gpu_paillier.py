@@ -180,3 +180,63 @@ def test_autotune_records_and_stays_exact(env):
     m = W.plaintexts_u64(300, seed=8)
     ct = pc2.encrypt(ctx, kg, torch.from_numpy(m.view(np.int64)).cuda(), SEED, STREAM)
     assert pc2.tiled_to_ints(ctx, ct, 3, 2 * kg.limbs) == _oracle_ct(ko, m[:3])
+
+
+def test_4096_bit_paths_bit_exact(env):
+    """4096-bit n, the largest key of the paper's evaluation: key-owner
+    encryption at every built lane count with the CRT halves one after the
+    other and in parallel, the public path, decryption (64-bit and full-width
+    plaintexts) and the homomorphic operations, against the oracle."""
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, 4096, seed=4)
+    assert kg.limbs == 128
+    count = 34                      # one full tile and a ragged tail
+    m = W.plaintexts_u64(count, seed=41)
+    m[0], m[1] = 0, np.uint64(2**64 - 1)
+    dm = torch.from_numpy(m.view(np.int64)).cuda()
+    ref = _oracle_ct(ko, m, e0=3)
+    L2 = 2 * kg.limbs
+    try:
+        for lanes in (2, 4, 8):
+            for split in (1, 2):
+                pc2.set_lanes(ctx, lanes)
+                pc2.set_split(ctx, split)
+                ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM, e0=3)
+                assert pc2.tiled_to_ints(ctx, ct, count, L2) == ref, (lanes, split)
+                dec = pc2.tiled_to_ints(ctx, pc2.decrypt(ctx, kg, ct, count), count, kg.limbs)
+                assert dec == [int(x) for x in m], (lanes, split)
+    finally:
+        pc2.set_lanes(ctx, 0)
+        pc2.set_split(ctx, 0)
+    ctp = pc2.encrypt(ctx, kg, dm[:5], SEED, STREAM, e0=3, public=True)
+    assert pc2.tiled_to_ints(ctx, ctp, 5, L2) == ref[:5]
+    mw = W.uniform_below(ko.n, 3, 5) + [ko.n - 1]
+    cw = O.encrypt(ko, mw, [O.r_of(ko, 9, 1, e) for e in range(len(mw))])
+    dcw = pc2.ints_to_tiled(ctx, cw, L2)
+    assert pc2.tiled_to_ints(ctx, pc2.decrypt(ctx, kg, dcw, len(mw)), len(mw), kg.limbs) == mw
+    a, b = pc2.ints_to_tiled(ctx, ref[:4], L2), dcw
+    assert pc2.tiled_to_ints(ctx, pc2.hom_add(ctx, kg, a, b, 4), 4, L2) == O.hom_add(ko, ref[:4], cw)
+    k = np.array([0, 1, 3, 2**64 - 1], dtype=np.uint64)
+    out = pc2.hom_scal(ctx, kg, a, torch.from_numpy(k.view(np.int64)).cuda(), 4)
+    assert pc2.tiled_to_ints(ctx, out, 4, L2) == O.hom_scal(ko, ref[:4], [int(x) for x in k])
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("nbits,count", [(512, 37), (2048, 9), (4096, 3)])
+def test_hom_scal_wide_bit_exact(env, nbits, count):
+    """Definition 2 with full-width scalars (the plain power mod n^2) against the oracle."""
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, nbits, seed=8)
+    L2 = 2 * kg.limbs
+    c = O.encrypt(ko, W.uniform_below(ko.n, count, 12), [O.r_of(ko, 4, 4, e) for e in range(count)])
+    ks = [0, 1, 2**nbits - 1] + W.uniform_below(ko.n, count - 3, 13)
+    dc, dk = pc2.ints_to_tiled(ctx, c, L2), pc2.ints_to_tiled(ctx, ks, kg.limbs)
+    out = pc2.hom_scal_wide(ctx, kg, dc, dk, count)
+    assert pc2.tiled_to_ints(ctx, out, count, L2) == O.hom_scal_wide(ko, c, ks)
+    for w in (4, 6):
+        ctx.set_window(w)
+        try:
+            out = pc2.hom_scal_wide(ctx, kg, dc, dk, count)
+        finally:
+            ctx.set_window(0)
+        assert pc2.tiled_to_ints(ctx, out, 2, L2) == O.hom_scal_wide(ko, c[:2], ks[:2]), w

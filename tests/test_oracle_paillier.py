@@ -188,3 +188,17 @@ def test_lifted_route_identity(nbits):
     r = P.r_of(k, 12, 3, 7)
     cp = pow(pow(r % k.p, k.q % (k.p - 1), k.p), k.p, k.p ** 2) * (1 + 5 * k.n) % (k.p ** 2)
     assert cp == P.encrypt(k, [5], [r])[0] % (k.p ** 2)
+
+
+def test_hom_scal_wide_pins():
+    # Definition 2 with k in Z_n: the oracle's binary exponentiation against
+    # Python's pow, the decryption identity D(E(a)^k) = k a mod n, and k = 0, 1.
+    k = _key(512, seed=10)
+    rng = random.Random(11)
+    a = [rng.randrange(k.n) for _ in range(4)]
+    c = P.encrypt(k, a, [P.r_of(k, 5, 6, e) for e in range(4)])
+    ks = [0, 1, k.n - 1, rng.randrange(k.n)]
+    out = P.hom_scal_wide(k, c, ks)
+    assert out == [pow(ci, ki, k.n2) for ci, ki in zip(c, ks)]
+    assert out[0] == 1 and out[1] == c[1]
+    assert P.decrypt(k, out) == [ki * ai % k.n for ai, ki in zip(a, ks)]
