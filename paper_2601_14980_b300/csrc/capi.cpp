@@ -77,6 +77,12 @@ const int* lane_set(int op, int limbs, int* n) {
       case 32: case 64: *n = 4; return s1248;
       case 128: case 192: *n = 2; return s48;
     }
+  } else if (op == OP_N2) {  // first entry = lanes_for(limbs), the large-batch choice
+    switch (limbs) {
+      case 16: *n = 3; return s124;
+      case 32: case 64: *n = 4; return s1248;
+      case 128: case 192: case 256: *n = 2; return s48;
+    }
   } else {
     switch (limbs) {
       case 8: *n = 3; return s124;
@@ -97,11 +103,15 @@ static int log2_bucket(size_t count) {
 LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
   int n = 0;
   const int* set = lane_set(op, limbs, &n);
-  const bool can_split = op != OP_MATVEC;
-  const double cap = (double)ctx->sms * 384.0;  // resident threads of one wave (about 384 per SM)
+  const bool can_split = op == OP_ENC_CRT || op == OP_DEC;
+  // resident threads of one wave: the kernels' launch bound (CTAs per SM for
+  // these limbs and lanes); the matvec kernels about 384 per SM
+  auto cap = [&](int T) {
+    return (double)ctx->sms * (op == OP_MATVEC ? 384.0 : (double)kThreads * min_blocks(limbs, T));
+  };
   auto auto_split = [&](int T) {
     if (!can_split || ctx->split == 1) return false;
-    return ctx->split == 2 || (double)count * 2 * T <= cap;
+    return ctx->split == 2 || (double)count * 2 * T <= cap(T);
   };
   if (ctx->lanes)
     for (int i = 0; i < n; ++i)
@@ -120,7 +130,7 @@ LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
       if (s && (!can_split || ctx->split == 1)) continue;
       if (!s && ctx->split == 2 && can_split) continue;
       const int le = set[i] * (s ? 2 : 1);
-      if ((double)count * le > cap) continue;
+      if ((double)count * le > cap(set[i])) continue;
       if (le > best_lanes || (le == best_lanes && s)) {
         best = LaneCfg{set[i], 0, s != 0};
         best_lanes = le;
@@ -143,6 +153,24 @@ static int with_crt_lanes(int T, Fn fn) {
     case 2: if constexpr (crt_has<Lh, 2>()) return fn(std::integral_constant<int, 2>()); break;
     case 4: if constexpr (crt_has<Lh, 4>()) return fn(std::integral_constant<int, 4>()); break;
     case 8: if constexpr (crt_has<Lh, 8>()) return fn(std::integral_constant<int, 8>()); break;
+  }
+  return PC2_EUNSUPPORTED;
+}
+
+template <int L2, int T>
+constexpr bool n2_has() {
+  return (L2 == 16 && T <= 4) || ((L2 == 32 || L2 == 64) && T <= 8) ||
+         ((L2 == 128 || L2 == 192 || L2 == 256) && (T == 4 || T == 8));
+}
+// Calls fn(std::integral_constant<int, T>) with the lane count picked for a
+// power or product mod n^2 over `count` elements.
+template <int L2, class Fn>
+static int with_n2_lanes(pc2_ctx* ctx, size_t count, Fn fn) {
+  switch (pick_config(ctx, OP_N2, L2, count).T) {
+    case 1: if constexpr (n2_has<L2, 1>()) return fn(std::integral_constant<int, 1>()); break;
+    case 2: if constexpr (n2_has<L2, 2>()) return fn(std::integral_constant<int, 2>()); break;
+    case 4: if constexpr (n2_has<L2, 4>()) return fn(std::integral_constant<int, 4>()); break;
+    case 8: if constexpr (n2_has<L2, 8>()) return fn(std::integral_constant<int, 8>()); break;
   }
   return PC2_EUNSUPPORTED;
 }
@@ -236,7 +264,9 @@ static int enc_pub(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->stream = stream;
   P->e0 = e0;
   P->mwords = mw ? L2 / 2 : 2;
-  return launch_enc_pub<L2, lanes_for(L2)>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+  return with_n2_lanes<L2>(ctx, count, [&](auto tt) {
+    return launch_enc_pub<L2, decltype(tt)::value>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st);
+  });
 }
 
 template <int Lh>
@@ -283,7 +313,9 @@ static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs
     std::unique_ptr<HomParams<L2>> P(new (std::nothrow) HomParams<L2>(*P0));
     if (!P) return PC2_ENOMEM;
     for (int i = 0; i < k; ++i) P->src[i] = ops[i];
-    rc = launch_hom_sum<L2, lanes_for(L2)>(*P, count, out, ctx->sms, st, base);
+    rc = with_n2_lanes<L2>(ctx, count, [&](auto tt) {
+      return launch_hom_sum<L2, decltype(tt)::value>(*P, count, out, ctx->sms, st, base);
+    });
     if (rc) return rc;
     first = false;
   }
@@ -328,7 +360,9 @@ static int hom_scal(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, const 
   auto P = cached<HomParams<L2>>(key, KIND_HOM + 1, w, [&](HomParams<L2>& p) { return make_hom<L2>(*key, w, 1, p); },
                                  &rc);
   if (!P) return rc;
-  return launch_hom_scal<L2, lanes_for(L2)>(*P, ct, k, count, out, ctx_scratch, ctx, ctx->sms, st);
+  return with_n2_lanes<L2>(ctx, count, [&](auto tt) {
+    return launch_hom_scal<L2, decltype(tt)::value>(*P, ct, k, count, out, ctx_scratch, ctx, ctx->sms, st);
+  });
 }
 
 // Window of a full-width scalar: the context's width clamped to 4..6, else 5.
@@ -340,7 +374,9 @@ static int hom_scal_wide(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, c
   auto P = cached<HomParams<L2>>(key, KIND_HOM + 1, w, [&](HomParams<L2>& p) { return make_hom<L2>(*key, w, 1, p); },
                                  &rc);
   if (!P) return rc;
-  return launch_hom_scal_wide<L2, lanes_for(L2)>(*P, ct, kw, count, out, ctx_scratch, ctx, ctx->sms, st);
+  return with_n2_lanes<L2>(ctx, count, [&](auto tt) {
+    return launch_hom_scal_wide<L2, decltype(tt)::value>(*P, ct, kw, count, out, ctx_scratch, ctx, ctx->sms, st);
+  });
 }
 
 }  // namespace pc2

@@ -45,7 +45,7 @@ int hom_add_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* a, const uint32
 int decrypt_at(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t count, uint32_t* out, cudaStream_t st,
                size_t base);
 
-enum { OP_ENC_CRT = 0, OP_DEC = 1, OP_MATVEC = 2 };
+enum { OP_ENC_CRT = 0, OP_DEC = 1, OP_MATVEC = 2, OP_N2 = 3 };  // OP_N2: powers and products mod n^2
 
 // Launch configuration of one call: lanes per element, window width (0 = key
 // default) and whether the two CRT halves run in parallel (split, T > 1).

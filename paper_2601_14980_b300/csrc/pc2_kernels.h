@@ -46,6 +46,21 @@ int launch_hom_scal_wide(const HomParams<L2>& P, const uint32_t* ct, const uint3
 int launch_pack(const uint32_t* canon, size_t count, int Lc, uint32_t* tiled, int sms, cudaStream_t st);
 int launch_unpack(const uint32_t* tiled, size_t count, int Lc, uint32_t* canon, int sms, cudaStream_t st);
 
+// Resident CTAs per SM each kernel is compiled for: the register budget of
+// 65536 / (128 * blocks) must hold two limb segments (three when the modulus
+// segment lives in registers, T > 1) plus bookkeeping.  Measured on B300 with
+// squaring loops: L=64, T=1 at 3 CTAs/SM (152 registers) reaches 18.0
+// 32x32->64 products per clock per SM; L=96, T=2 at 2 CTAs 16.3; L=128, T=4 at
+// 3 CTAs 17.0.  Keeping the budget
+// tight stops the compiler from hoisting the modulus words (constant-bank
+// operands) into registers.
+constexpr int min_blocks(int L, int T) {
+  const int S = L / T;
+  const int regs = T == 1 ? 2 * S + 24 : 3 * S + 40;
+  const int b = 65536 / (kThreads * regs);
+  return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
 // Lanes per element for each modulus width: the row core keeps a segment of
 // the multiplicand and of the accumulator in registers (plus the modulus
 // segment when T > 1); wider operands are split across lanes.

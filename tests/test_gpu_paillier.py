@@ -240,3 +240,41 @@ def test_hom_scal_wide_bit_exact(env, nbits, count):
         finally:
             ctx.set_window(0)
         assert pc2.tiled_to_ints(ctx, out, 2, L2) == O.hom_scal_wide(ko, c[:2], ks[:2]), w
+
+
+@pytest.mark.parametrize("nbits", [256, 512, 1024, 2048])
+def test_n2_ops_lanes_bit_identical(env, nbits):
+    """Public encryption, products, 64-bit and full-width scalar powers mod n^2
+    give the oracle's results at every lane count (forced; sizes without a
+    lane count fall back to the automatic choice)."""
+    torch, pc2, ctx = env
+    kg, ko = _keys(pc2, nbits, seed=9)
+    count, L2 = 37, 2 * kg.limbs
+    m = W.plaintexts_u64(count, seed=nbits + 3)
+    dm = torch.from_numpy(m.view(np.int64)).cuda()
+    ref_ct = _oracle_ct(ko, m)
+    c2 = O.encrypt(ko, W.uniform_below(ko.n, count, 14), [O.r_of(ko, 2, 2, e) for e in range(count)])
+    k64 = np.array([0, 1, 2**64 - 1] + W.uniform_below(2**64, count - 3, 15), dtype=np.uint64)
+    kw = [0, 1, 2**nbits - 1] + W.uniform_below(ko.n, count - 3, 16)
+    ref_add = O.hom_add(ko, ref_ct, c2)
+    ref_sum = O.hom_sum(ko, [ref_ct, c2, ref_ct])
+    ref_scal = O.hom_scal(ko, ref_ct, [int(x) for x in k64])
+    ref_wide = O.hom_scal_wide(ko, ref_ct, kw)
+    d1, d2 = pc2.ints_to_tiled(ctx, ref_ct, L2), pc2.ints_to_tiled(ctx, c2, L2)
+    dk64 = torch.from_numpy(k64.view(np.int64)).cuda()
+    dkw = pc2.ints_to_tiled(ctx, kw, kg.limbs)
+    try:
+        for lanes in (1, 2, 4, 8):
+            pc2.set_lanes(ctx, lanes)
+            ct = pc2.encrypt(ctx, kg, dm, SEED, STREAM, public=True)
+            assert pc2.tiled_to_ints(ctx, ct, count, L2) == ref_ct, lanes
+            assert pc2.tiled_to_ints(ctx, pc2.hom_add(ctx, kg, d1, d2, count), count, L2) == ref_add, lanes
+            out = pc2.hom_sum(ctx, kg, torch.cat([d1, d2, d1]), 3, count)
+            assert pc2.tiled_to_ints(ctx, out, count, L2) == ref_sum, lanes
+            out = pc2.hom_scal(ctx, kg, d1, dk64, count)
+            assert pc2.tiled_to_ints(ctx, out, count, L2) == ref_scal, lanes
+            out = pc2.hom_scal_wide(ctx, kg, d1, dkw, count)
+            assert pc2.tiled_to_ints(ctx, out, count, L2) == ref_wide, lanes
+    finally:
+        pc2.set_lanes(ctx, 0)
+    assert ctx.status() == 0
