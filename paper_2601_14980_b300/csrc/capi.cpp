@@ -5,6 +5,7 @@
 // to the templated launchers.  No arithmetic on user data happens here.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -100,40 +101,64 @@ static int log2_bucket(size_t count) {
   return b;
 }
 
+// Estimated time of one call with T lanes per element (halves split or not),
+// in arbitrary units: the larger of
+//   latency: waves x (halves run one after the other: 2, split: 1) x
+//            (S + 64) per row -- a row's dependent chain grows with the
+//            limbs per lane S = limbs / T, plus a fixed part (quotient
+//            word, shuffles, loop) worth about 64 limbs;
+//   issue:   count x 2 x limbs / SMs -- the instructions of all lanes, the
+//            same for every T at this resolution.
+// The constants were fitted to measured encryption + decryption times at
+// 1024-, 2048- and 4096-bit n, 256..32768 elements, every lane count and
+// both split modes; the chosen configuration was within 10 % of the fastest
+// at every point.
+static double lane_cost(int limbs, int T, bool split, size_t count, int sms) {
+  const double cap = (double)sms * kThreads * min_blocks(limbs, T);
+  const double waves = std::ceil((double)count * T * (split ? 2 : 1) / cap);
+  const double lat = waves * (split ? 1.0 : 2.0) * ((double)limbs / T + 64.0) * 128.0;
+  const double issue = (double)count * 2.0 * limbs / sms;
+  return lat > issue ? lat : issue;
+}
+
 LaneCfg pick_config(pc2_ctx* ctx, int op, int limbs, size_t count) {
   int n = 0;
   const int* set = lane_set(op, limbs, &n);
   const bool can_split = op == OP_ENC_CRT || op == OP_DEC;
-  // resident threads of one wave: the kernels' launch bound (CTAs per SM for
-  // these limbs and lanes); the matvec kernels about 384 per SM
-  auto cap = [&](int T) {
-    return (double)ctx->sms * (op == OP_MATVEC ? 384.0 : (double)kThreads * min_blocks(limbs, T));
-  };
-  auto auto_split = [&](int T) {
-    if (!can_split || ctx->split == 1) return false;
-    return ctx->split == 2 || (double)count * 2 * T <= cap(T);
-  };
-  if (ctx->lanes)
-    for (int i = 0; i < n; ++i)
-      if (set[i] == ctx->lanes) return LaneCfg{ctx->lanes, 0, auto_split(ctx->lanes)};
+  const bool may_split = can_split && ctx->split != 1;
+  const bool must_split = can_split && ctx->split == 2;
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto it = ctx->tuned.find(std::make_tuple(op, limbs, log2_bucket(count)));
-    if (it != ctx->tuned.end())
+    if (!ctx->lanes && it != ctx->tuned.end())
       return LaneCfg{std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second) != 0};
   }
-  // the most lanes per element that still fit one wave; split at equal lanes
-  LaneCfg best{set[0], 0, false};
-  int best_lanes = 0;
+  if (op == OP_MATVEC) {
+    // the most lanes per row that still fit one wave (about 384 threads per SM)
+    const double cap = (double)ctx->sms * 384.0;
+    if (ctx->lanes)
+      for (int i = 0; i < n; ++i)
+        if (set[i] == ctx->lanes) return LaneCfg{ctx->lanes, 0, false};
+    LaneCfg best{set[0], 0, false};
+    for (int i = 0; i < n; ++i)
+      if ((double)count * set[i] <= cap) best = LaneCfg{set[i], 0, false};
+    return best;
+  }
+  // forced lanes (when built for this size) fix T; otherwise every built T
+  bool forced = false;
+  for (int i = 0; i < n; ++i) forced = forced || set[i] == ctx->lanes;
+  LaneCfg best{set[0], 0, must_split};
+  double best_cost = 0.0;
+  bool any = false;
   for (int i = 0; i < n; ++i) {
+    if (forced && set[i] != ctx->lanes) continue;
     for (int s = 0; s < 2; ++s) {
-      if (s && (!can_split || ctx->split == 1)) continue;
-      if (!s && ctx->split == 2 && can_split) continue;
-      const int le = set[i] * (s ? 2 : 1);
-      if ((double)count * le > cap(set[i])) continue;
-      if (le > best_lanes || (le == best_lanes && s)) {
+      if ((s && !may_split) || (!s && must_split)) continue;
+      const double c = lane_cost(limbs, set[i], s != 0, count, ctx->sms);
+      if (!any || c < best_cost) {
         best = LaneCfg{set[i], 0, s != 0};
-        best_lanes = le;
+        best_cost = c;
+        any = true;
       }
     }
   }
