@@ -23,10 +23,9 @@
  *    (element e at words [e*limbs, (e+1)*limbs)).
  *  - Key sizes: n of 256, 512, 1024, 2048, 3072 or 4096 bits (the paper's
  *    evaluation uses 1024, 2048 and 4096).  Plaintexts have nbits/32 limbs,
- *    ciphertexts nbits/16 limbs.  The encrypted matvec and the ADMM objects
- *    built on it (pc2_hom_matvec, pc2_admm_*) take keys up to 3072 bits, the
- *    batched round (pc2_batch_*) the five sizes up to 3072 bits, the server
- *    512- and 2048-bit keys; other calls return PC2_EUNSUPPORTED.
+ *    ciphertexts nbits/16 limbs.  The batched round (pc2_batch_*) takes the
+ *    five sizes up to 3072 bits and the server 512- and 2048-bit keys (other
+ *    sizes return PC2_EUNSUPPORTED); every other call takes all six.
  *  - Scratch: a context owns device scratch memory and grows it on the first
  *    call that needs more (cudaMalloc; synchronises the device).  Call
  *    pc2_ctx_reserve() first to avoid growth inside timed regions or stream

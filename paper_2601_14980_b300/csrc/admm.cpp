@@ -119,7 +119,7 @@ static int matvec_launch_t(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
 }
 
 // Lanes per row of the matvec: the count picked at creation (built sets:
-// 1, 2, 4 for 16 limbs; 1, 2, 4, 8 for 32 and 64; 4, 8 for 128 and 192).
+// 1, 2, 4 for 16 limbs; 1, 2, 4, 8 for 32 and 64; 4, 8 for 128, 192 and 256).
 template <int L2>
 static int matvec_launch(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
   switch (A->mv_T) {
@@ -150,6 +150,7 @@ static int dispatch_matvec(pc2_admm* A, int tile0, int ntl, cudaStream_t st) {
     case 64: return matvec_launch<64>(A, tile0, ntl, st);
     case 128: return matvec_launch<128>(A, tile0, ntl, st);
     case 192: return matvec_launch<192>(A, tile0, ntl, st);
+    case 256: return matvec_launch<256>(A, tile0, ntl, st);
     default: return PC2_EUNSUPPORTED;
   }
 }
@@ -160,6 +161,7 @@ static int dispatch_to_mont(pc2_admm* A, cudaStream_t st) {
     case 64: return to_mont_launch<64>(A, st);
     case 128: return to_mont_launch<128>(A, st);
     case 192: return to_mont_launch<192>(A, st);
+    case 256: return to_mont_launch<256>(A, st);
     default: return PC2_EUNSUPPORTED;
   }
 }
@@ -557,6 +559,7 @@ int pc2_hom_matvec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_alpha, co
     case 64: return block_matvec_any<64>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
     case 128: return block_matvec_any<128>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
     case 192: return block_matvec_any<192>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
+    case 256: return block_matvec_any<256>(ctx, key, d_alpha, d_s, d_K, (int)n, kb, d_out, st);
     default: return PC2_EUNSUPPORTED;
   }
 }

@@ -76,7 +76,7 @@ const int* lane_set(int op, int limbs, int* n) {
     switch (limbs) {
       case 16: *n = 3; return s124;
       case 32: case 64: *n = 4; return s1248;
-      case 128: case 192: *n = 2; return s48;
+      case 128: case 192: case 256: *n = 2; return s48;
     }
   } else if (op == OP_N2) {  // first entry = lanes_for(limbs), the large-batch choice
     switch (limbs) {

@@ -144,7 +144,7 @@ def test_quantize_entry_point(env):
 
 
 @pytest.mark.parametrize("nbits,lanes", [(256, 1), (256, 4), (512, 2), (512, 8), (1024, 1), (1024, 4),
-                                         (2048, 2), (2048, 8), (3072, 4), (3072, 8)])
+                                         (2048, 2), (2048, 8), (3072, 4), (3072, 8), (4096, 4), (4096, 8)])
 def test_lanes_per_element_rounds_bit_exact(env, nbits, lanes):
     """Every built lane count of the matvec (and of encryption/decryption where built) gives the oracle's iterates."""
     torch, pc2, ctx = env

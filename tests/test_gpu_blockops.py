@@ -59,7 +59,7 @@ def test_decode_matvec_equals_oracle_decode(env):
     assert ctx.status() == 0
 
 
-@pytest.mark.parametrize("nbits,n,kbits", [(512, 37, 12), (1024, 70, 28), (2048, 20, 5)])
+@pytest.mark.parametrize("nbits,n,kbits", [(512, 37, 12), (1024, 70, 28), (2048, 20, 5), (4096, 6, 5)])
 def test_hom_matvec_block_equals_oracle(env, nbits, n, kbits):
     torch, pc2, ctx = env
     p, q = W.primes(nbits, 4)
