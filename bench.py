@@ -433,6 +433,64 @@ def run_table2(dev, count: int = 9000, trials: int = 10):
             "unit": "ops/s", "rows": rows}
 
 
+def run_hbm(dev, n: int = 1 << 27, n_dec: int = 1 << 24, reps: int = 5):
+    """Achieved HBM bandwidth of the memory-bound steps on vectors far larger
+    than L2 (each input 1 GiB at n = 2^27): quantize (Gamma2, Eq. (et21)),
+    dequantize, the z/v update (Eqs. (ty32), (u78)) and the exact decode of
+    Theorem 1 on 1024-bit decrypted rows.  GB/s = algorithmic bytes (inputs
+    read once, outputs written once) / CUDA-event time, mean of `reps`."""
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    ctx = pc2.Context(dev)
+    st = torch.cuda.current_stream()
+    g = torch.Generator(device=dev).manual_seed(5)
+    u = torch.randn(n, generator=g, dtype=torch.float64, device=dev)
+    q = torch.empty(n, dtype=torch.int64, device=dev)
+    x = torch.randn(n, generator=g, dtype=torch.float64, device=dev) * 0.02
+    z = torch.zeros(n, dtype=torch.float64, device=dev)
+    v = torch.randn(n, generator=g, dtype=torch.float64, device=dev) * 0.02
+    limbs = 32
+    # decrypted rows below 2^62 (words 0, 1; the other words zero, as the decode expects),
+    # tiled: words 0..3 of a tile's 32 elements form its first 128-word slab
+    D = torch.zeros(pc2.tiled_words(n_dec, limbs), dtype=torch.int32, device=dev)
+    lo = D.view(-1, limbs // 4, 32, 4)[:, 0]
+    lo[:, :, 0] = torch.randint(-(1 << 31), 1 << 31, lo[:, :, 0].shape, generator=g, dtype=torch.int32, device=dev)
+    lo[:, :, 1] = torch.randint(0, 1 << 30, lo[:, :, 1].shape, generator=g, dtype=torch.int32, device=dev)
+    brow = torch.randint(0, 1 << 30, (n_dec,), generator=g, dtype=torch.int64, device=dev)
+    asum = torch.randint(0, 1 << 33, (n_dec,), generator=g, dtype=torch.int64, device=dev)
+    nk = torch.full((n_dec,), 64, dtype=torch.int32, device=dev)
+    xd = torch.empty(n_dec, dtype=torch.float64, device=dev)
+    steps = {
+        "quantize": (lambda: pc2.quantize(ctx, u, -8.0, 8.0, 24, 2, out=q), 16 * n),
+        "dequantize": (lambda: pc2.dequantize(ctx, q, -8.0, 24, 2, out=u), 16 * n),
+        "zv_update": (lambda: pc2.zv_update(ctx, x, z, v, 0.01), 40 * n),
+        "decode_matvec": (lambda: pc2.decode_matvec(ctx, D, limbs, n_dec, brow, asum, nk, -8.0, 24, out=xd),
+                          (4 * limbs + 8 + 8 + 4 + 8) * n_dec),
+    }
+    peak = _peaks().get("hbm_gbs")
+    out = {}
+    for name, (fn, nbytes) in steps.items():
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.mean(ms)
+        gbs = nbytes / (t / 1e3) / 1e9
+        out[name] = {"elements": n if name != "decode_matvec" else n_dec, "bytes": nbytes, "ms": t, "gb_s": gbs,
+                     "frac_of_measured_hbm": gbs / peak if peak else None}
+    del u, q, x, z, v, D, brow, asum, nk, xd
+    torch.cuda.empty_cache()
+    return {"peak_gb_s": peak, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)", "steps": out}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -563,6 +621,7 @@ def run_gpu(args):
         "batch": None if args.no_batch else run_batch(dev, args.batch_rounds),
         "serve": None if args.no_serve else run_serve(dev),
         "table2": None if args.no_table2 else run_table2(dev),
+        "hbm": None if args.no_hbm else run_hbm(dev, n=args.hbm_elems, n_dec=min(args.hbm_elems, 1 << 24)),
         "admm_full": run_admm_full(dev) if args.admm_full else None,
     }
     print(json.dumps(line))
@@ -597,6 +656,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-table2", action="store_true", help="skip the Table II operations at 1024/2048/4096 bits")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the bandwidth of the memory-bound steps")
+    ap.add_argument("--hbm-elems", type=int, default=1 << 27, help="vector length of the bandwidth section")
     ap.add_argument("--admm-full", action="store_true", help="also time the full-scale 3072-bit ADMM (about 2 min)")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")

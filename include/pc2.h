@@ -193,6 +193,12 @@ int pc2_dequantize(pc2_ctx* ctx, const uint64_t* d_q, size_t n, double zmin, int
 int pc2_decode_matvec(pc2_ctx* ctx, const uint32_t* d_D, int limbs, size_t n, const long long* d_brow,
                       const unsigned long long* d_asum, const int* d_nk, double zmin, int log2_scale, double* d_x,
                       pc2_stream_t stream);
+/* The master's update, Eqs. (ty32) and (u78), elementwise in IEEE double
+ * without contraction: a = v_i + x_i, z_i = S_kappa(a) (a - kappa above kappa,
+ * a + kappa below -kappa, else 0), v_i = a - z_i.  d_z and d_v are updated in
+ * place; n < 2^31. */
+int pc2_zv_update(pc2_ctx* ctx, const double* d_x, double* d_z, double* d_v, size_t n, double kappa,
+                  pc2_stream_t stream);
 
 /* ---- encrypted matrix-vector product ----------------------------------- *
  * Eq. (itq2) on one n x n block: out_i = alpha_i (+) sum_j K_ij (x) s_j =

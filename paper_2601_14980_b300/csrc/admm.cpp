@@ -531,6 +531,13 @@ int pc2_dequantize(pc2_ctx* ctx, const uint64_t* d_q, size_t n, double zmin, int
   return launch_dequantize(d_q, n, zmin, inv, d_u, ctx->sms, (cudaStream_t)stream);
 }
 
+int pc2_zv_update(pc2_ctx* ctx, const double* d_x, double* d_z, double* d_v, size_t n, double kappa,
+                  pc2_stream_t stream) {
+  if (!ctx || n > (size_t)0x7fffffff || (n && (!d_x || !d_z || !d_v)) || !(kappa >= 0.0)) return PC2_EINVAL;
+  if (!n) return PC2_OK;
+  return launch_zv_update(d_x, d_z, d_v, (int)n, kappa, ctx->sms, (cudaStream_t)stream);
+}
+
 int pc2_decode_matvec(pc2_ctx* ctx, const uint32_t* d_D, int limbs, size_t n, const long long* d_brow,
                       const unsigned long long* d_asum, const int* d_nk, double zmin, int log2_scale, double* d_x,
                       pc2_stream_t stream) {

@@ -617,10 +617,17 @@ class Server:
 
 
 _dequantize = _sig("pc2_dequantize", [_vp, _vp, _sz, ctypes.c_double, _i, _i, _vp, _vp])
+_zv_update = _sig("pc2_zv_update", [_vp, _vp, _vp, _vp, _sz, ctypes.c_double, _vp])
 _decode_matvec = _sig("pc2_decode_matvec", [_vp, _vp, _i, _sz, _vp, _vp, _vp, ctypes.c_double, _i, _vp, _vp])
 _hom_matvec = _sig("pc2_hom_matvec", [_vp, _vp, _vp, _vp, _vp, _sz, _i, _vp, _vp])
 _admm_save = _sig("pc2_admm_save", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32)])
 _admm_load = _sig("pc2_admm_load", [_vp, _vp, _vp, _vp, _u32])
+
+
+def zv_update(ctx: Context, x, z, v, kappa: float, stream=None):
+    """Eqs. (ty32), (u78) in place on float64 tensors: z = S_kappa(v + x), v = v + x - z."""
+    n = int(x.numel())
+    _check(_zv_update(ctx.h, _ptr(x), _ptr(z), _ptr(v), n, kappa, _stream(stream)), "pc2_zv_update")
 
 
 def dequantize(ctx: Context, q, zmin: float, log2_scale: int, gamma: int = 2, out=None, stream=None):

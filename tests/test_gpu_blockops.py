@@ -106,3 +106,21 @@ def test_admm_host_checkpoint_round_trip(env):
         assert torch.equal(u, w)
     ref = O.quantized_admm(st, L.lam, L.rho, 4, QP)
     assert np.array_equal(b.get()[2].cpu().numpy(), ref.v[3])
+
+
+def test_zv_update_equals_oracle(env):
+    """Eqs. (ty32), (u78) elementwise, bit-exact against the oracle's update,
+    with v + x landing exactly on +-kappa, on 0 and inside the dead zone."""
+    torch, pc2, ctx = env
+    rng = np.random.default_rng(3)
+    n, kappa = 1000, 0.01
+    x = rng.standard_normal(n) * 0.02
+    v = rng.standard_normal(n) * 0.02
+    x[:4] = [kappa, -kappa, 0.0, 0.004]
+    v[:4] = 0.0
+    z = rng.standard_normal(n)
+    z_ref = O.soft_threshold(v + x, kappa)
+    v_ref = v + x - z_ref
+    dx, dz, dv = (torch.from_numpy(a.copy()).cuda() for a in (x, z, v))
+    pc2.zv_update(ctx, dx, dz, dv, kappa)
+    assert np.array_equal(dz.cpu().numpy(), z_ref) and np.array_equal(dv.cpu().numpy(), v_ref)
