@@ -118,10 +118,26 @@ __global__ void k_dis_xupdate(const double* __restrict__ alpha, const double* __
 
 // ------------------------------------------------------------------ inverse quantization
 // u = q * (1/S or 1/S^2) + zmin in IEEE double (exact for the quantizer's outputs).
+// inv_scale = 2^-k, so q * inv_scale is exact; for q < 2^53 its double is
+// assembled from q's bits (integer instructions), above that by the FP64
+// conversion and product.  Then one rounded addition of zmin.
 __global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zmin, double inv_scale,
                              double* __restrict__ u) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    u[i] = __dadd_rn(__dmul_rn((double)q[i], inv_scale), zmin);
+  const int k = 1023 - (int)((__double_as_longlong(inv_scale) >> 52) & 0x7ff);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t x = q[i];
+    double p;
+    if (x == 0u) {
+      p = 0.0;
+    } else if (x < (1ull << 53)) {
+      const int lz = __clzll((long long)x);  // >= 11
+      const uint64_t mant = (x << (lz - 11)) & ((1ull << 52) - 1u);
+      p = __longlong_as_double(((long long)(1086 - lz - k) << 52) | (long long)mant);
+    } else {
+      p = __dmul_rn((double)x, inv_scale);
+    }
+    u[i] = __dadd_rn(p, zmin);
+  }
 }
 
 // The exact decode of Theorem 1 for one matvec row per thread (no z/v update):

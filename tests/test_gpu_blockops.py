@@ -124,3 +124,24 @@ def test_zv_update_equals_oracle(env):
     dx, dz, dv = (torch.from_numpy(a.copy()).cuda() for a in (x, z, v))
     pc2.zv_update(ctx, dx, dz, dv, kappa)
     assert np.array_equal(dz.cpu().numpy(), z_ref) and np.array_equal(dv.cpu().numpy(), v_ref)
+
+
+def test_quantize_ties_edges_and_flags(env):
+    """Eq. (et21) at exact half-way points (round half to even), at the range
+    ends and just inside them, for both quantizers, against the oracle; and the
+    clamp and flag for values outside the range, infinities and NaN."""
+    torch, pc2, ctx = env
+    k = QP.log2_scale
+    ties2 = [QP.zmin + (2 * j + 1) * 2.0 ** -(k + 1) for j in range(0, 4000, 7)]
+    ties1 = [QP.zmin + (2 * j + 1) * 2.0 ** -(2 * k + 1) for j in range(0, 4000, 7)]
+    edges = [QP.zmin, QP.zmax, QP.zmin + 2.0 ** -60, QP.zmax - 2.0 ** -40, QP.zmin - 0.5 * 2.0 ** -k, 0.0, -0.0]
+    for gamma, oq, vals in ((2, O.gamma2, ties2 + edges), (1, O.gamma1, ties1 + edges)):
+        u = np.array(vals)
+        q = pc2.quantize(ctx, torch.from_numpy(u).cuda(), QP.zmin, QP.zmax, k, gamma)
+        assert np.array_equal(q.cpu().numpy(), oq(u, QP)), gamma
+    assert ctx.status() == 0
+    bad = np.array([QP.zmax + 1.0, QP.zmin - 1.0, np.inf, -np.inf, np.nan, 1e300])
+    q = pc2.quantize(ctx, torch.from_numpy(bad).cuda(), QP.zmin, QP.zmax, k, 2).cpu().numpy()
+    delta = int(round((QP.zmax - QP.zmin) * 2 ** k))
+    assert q.tolist() == [delta, 0, delta, 0, 0, delta]
+    assert ctx.status() & pc2.ST_QUANT
