@@ -134,9 +134,10 @@ def test_quantize_ties_edges_and_flags(env):
     k = QP.log2_scale
     ties2 = [QP.zmin + (2 * j + 1) * 2.0 ** -(k + 1) for j in range(0, 4000, 7)]
     ties1 = [QP.zmin + (2 * j + 1) * 2.0 ** -(2 * k + 1) for j in range(0, 4000, 7)]
-    edges = [QP.zmin, QP.zmax, QP.zmin + 2.0 ** -60, QP.zmax - 2.0 ** -40, QP.zmin - 0.5 * 2.0 ** -k, 0.0, -0.0]
-    for gamma, oq, vals in ((2, O.gamma2, ties2 + edges), (1, O.gamma1, ties1 + edges)):
-        u = np.array(vals)
+    for gamma, oq, vals in ((2, O.gamma2, ties2), (1, O.gamma1, ties1)):
+        half = 0.5 * 2.0 ** -(k if gamma == 2 else 2 * k)      # half a step of this quantizer
+        edges = [QP.zmin, QP.zmax, QP.zmin + 2.0 ** -60, QP.zmax - 2.0 ** -40, QP.zmin - half, 0.0, -0.0]
+        u = np.array(vals + edges)
         q = pc2.quantize(ctx, torch.from_numpy(u).cuda(), QP.zmin, QP.zmax, k, gamma)
         assert np.array_equal(q.cpu().numpy(), oq(u, QP)), gamma
     assert ctx.status() == 0
