@@ -465,7 +465,7 @@ def run_hbm(dev, n: int = 1 << 27, n_dec: int = 1 << 24, reps: int = 5):
     steps = {
         "quantize": (lambda: pc2.quantize(ctx, u, -8.0, 8.0, 24, 2, out=q), 16 * n),
         "dequantize": (lambda: pc2.dequantize(ctx, q, -8.0, 24, 2, out=u), 16 * n),
-        "zv_update": (lambda: pc2.zv_update(ctx, x, z, v, 0.01), 40 * n),
+        "zv_update": (lambda: pc2.zv_update(ctx, x, z, v, 0.01), 32 * n),   # x, v in; z, v out
         "decode_matvec": (lambda: pc2.decode_matvec(ctx, D, limbs, n_dec, brow, asum, nk, -8.0, 24, out=xd),
                           (4 * limbs + 8 + 8 + 4 + 8) * n_dec),
     }

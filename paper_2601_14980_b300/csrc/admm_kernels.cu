@@ -26,10 +26,28 @@
 namespace pc2 {
 
 // ------------------------------------------------------------------ quantizer
+// Memory-bound elementwise kernels: each thread takes kUnroll elements one
+// grid stride apart per step and issues all their loads before any
+// arithmetic (more bytes in flight per SM than one load per thread).
+constexpr int kUnroll = 4;
+
 __global__ void k_quantize(const double* __restrict__ u, size_t n, double zmin, double scale, double qmax, int negate,
                            uint64_t* __restrict__ q, int* status, uint32_t* bitlen_or) {
   uint32_t acc = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
+    double x[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) x[k] = u[i + k * stride];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      const uint64_t v = quant(negate ? -x[k] : x[k], zmin, scale, qmax, status);
+      q[i + k * stride] = v;
+      acc |= (uint32_t)(v >> 32) ? 0xffffffffu : (uint32_t)v;
+    }
+  }
+  for (; i < n; i += stride) {
     const double x = negate ? -u[i] : u[i];
     const uint64_t v = quant(x, zmin, scale, qmax, status);
     q[i] = v;
@@ -90,8 +108,25 @@ __global__ void k_admm_update(const uint32_t* __restrict__ D, int Lh, int N, con
 
 __global__ void k_zv_update(const double* __restrict__ x, double* __restrict__ z, double* __restrict__ v, int N,
                             double kappa) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double zi = z[i], vi = v[i];
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * (long long)stride < N; i += kUnroll * stride) {
+    double xs[kUnroll], vs[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      xs[k] = x[i + k * stride];
+      vs[k] = v[i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; ++k) {
+      double zi = 0.0, vi = vs[k];
+      zv_update(xs[k], zi, vi, kappa);
+      z[i + k * stride] = zi;
+      v[i + k * stride] = vi;
+    }
+  }
+  for (; i < N; i += stride) {
+    double zi = 0.0, vi = v[i];
     zv_update(x[i], zi, vi, kappa);
     z[i] = zi;
     v[i] = vi;
@@ -124,8 +159,7 @@ __global__ void k_dis_xupdate(const double* __restrict__ alpha, const double* __
 __global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zmin, double inv_scale,
                              double* __restrict__ u) {
   const int k = 1023 - (int)((__double_as_longlong(inv_scale) >> 52) & 0x7ff);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t x = q[i];
+  auto one = [&](uint64_t x) {
     double p;
     if (x == 0u) {
       p = 0.0;
@@ -136,8 +170,18 @@ __global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zm
     } else {
       p = __dmul_rn((double)x, inv_scale);
     }
-    u[i] = __dadd_rn(p, zmin);
+    return __dadd_rn(p, zmin);
+  };
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
+    uint64_t xs[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) xs[j] = q[i + j * stride];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) u[i + j * stride] = one(xs[j]);
   }
+  for (; i < n; i += stride) u[i] = one(q[i]);
 }
 
 // The exact decode of Theorem 1 for one matvec row per thread (no z/v update):
