@@ -26,9 +26,9 @@
 namespace pc2 {
 
 // ------------------------------------------------------------------ quantizer
-// Memory-bound elementwise kernels: each thread takes kUnroll elements one
-// grid stride apart per step and issues all their loads before any
-// arithmetic (more bytes in flight per SM than one load per thread).
+// Memory-bound elementwise kernels (quantize, z/v update): each thread takes
+// kUnroll elements one grid stride apart per step and issues all their loads
+// before any arithmetic (more bytes in flight per SM than one load per thread).
 constexpr int kUnroll = 4;
 
 __global__ void k_quantize(const double* __restrict__ u, size_t n, double zmin, double scale, double qmax, int negate,
@@ -158,8 +158,11 @@ __global__ void k_dis_xupdate(const double* __restrict__ alpha, const double* __
 // conversion and product.  Then one rounded addition of zmin.
 __global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zmin, double inv_scale,
                              double* __restrict__ u) {
+  // one element per step: unrolled, the compiler predicates the rare FP64
+  // branch and runs it for every element (measured slower)
   const int k = 1023 - (int)((__double_as_longlong(inv_scale) >> 52) & 0x7ff);
-  auto one = [&](uint64_t x) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t x = q[i];
     double p;
     if (x == 0u) {
       p = 0.0;
@@ -170,18 +173,8 @@ __global__ void k_dequantize(const uint64_t* __restrict__ q, size_t n, double zm
     } else {
       p = __dmul_rn((double)x, inv_scale);
     }
-    return __dadd_rn(p, zmin);
-  };
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + (kUnroll - 1) * stride < n; i += kUnroll * stride) {
-    uint64_t xs[kUnroll];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) xs[j] = q[i + j * stride];
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) u[i + j * stride] = one(xs[j]);
+    u[i] = __dadd_rn(p, zmin);
   }
-  for (; i < n; i += stride) u[i] = one(q[i]);
 }
 
 // The exact decode of Theorem 1 for one matvec row per thread (no z/v update):
