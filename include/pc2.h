@@ -76,15 +76,18 @@ int pc2_ctx_status(pc2_ctx* ctx, pc2_stream_t stream, int* bits);
 /* Forces the sliding-window width (3..6) of subsequent exponentiations; 0 = automatic. */
 int pc2_ctx_set_window(pc2_ctx* ctx, int w);
 /* Forces the lanes per element (1, 2, 4, 8) of the exponentiation kernels where
- * that count is built for the operand size; 0 = automatic (autotuned entry for
- * the call's size class if any, else the largest lane count whose element
- * groups still fit in one resident wave: small batches get more lanes per
- * element and finish sooner). */
+ * that count is built for the operand size; 0 = automatic: the autotuned
+ * entry for the call's size class if any, else the lane count and split mode
+ * with the lowest estimated time (the larger of a latency term -- waves of
+ * resident element groups x halves run in sequence x (limbs per lane + 64)
+ * per Montgomery row -- and an issue term the same for every lane count),
+ * fitted to measured times: small batches get more lanes per element and
+ * finish sooner, large ones run one lane per element. */
 int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes);
 /* Runs the two CRT halves of each element's exponentiations in parallel
  * (one half per two warps of a CTA, recombined after a block barrier):
- * mode 0 automatic (when the doubled lanes still fit one resident wave),
- * 1 never, 2 always.  Results do not change. */
+ * mode 0 automatic (by the estimate of pc2_ctx_set_lanes), 1 never,
+ * 2 always.  Results do not change. */
 int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
 /* Autotuner: times every built lane count x split (on, off) x window
  * width (4..6) of key-owner encryption (ops bit 0) and/or decryption (bit 1)
