@@ -244,3 +244,23 @@ def test_exact_rowdot_split_equals_python_integers():
     assert O.exact_rowdot(b, a) == want        # split path (b.size > 2^16)
     small = b[:100, :50]
     assert O.exact_rowdot(small, a[:50]) == [sum(int(small[i, j]) * a[j] for j in range(50)) for i in range(100)]
+
+
+def test_precision_loss_falls_as_one_over_delta():
+    # The paper's experiment on the quantization's precision loss (a 3 x 3
+    # design, Delta swept over many decades): the private iterate differs from
+    # plaintext Dis-ADMM by O(1/Delta).  Here Delta = S (zmax - zmin) with
+    # S = 2^8 .. 2^28 (the Gamma1 scale S^2 Delta must stay below 2^63), 20
+    # rounds; the gap shrinks with every step of S and stays within a fixed
+    # multiple of 1/Delta.
+    L = W.lasso_small(seed=2, M=3, N=3, nnz=1, K=3, lam=0.01, rho=1.0)
+    st = O.dis_setup(L.A, L.y, W.node_sizes(3, 3), L.rho)
+    xp = O.dis_admm(st, L.lam, L.rho, 20)[0]
+    gaps = []
+    for k in (8, 12, 16, 20, 24, 28):
+        qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=k)
+        gap = float(np.max(np.abs(O.quantized_admm(st, L.lam, L.rho, 20, qp).x[-1] - xp)))
+        delta = 16.0 * 2.0 ** k
+        assert 0.5 <= gap * delta <= 64.0, (k, gap * delta)
+        gaps.append(gap)
+    assert all(b < a for a, b in zip(gaps, gaps[1:]))
