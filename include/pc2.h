@@ -411,8 +411,9 @@ int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, u
  *  - All calls share the one array: calls whose kernels overlap on a GPU
  *    (different streams, or different host threads) race and corrupt each
  *    other's results.  Order them on one stream.
+ *  - Keys of 256 to 3072 bits; PC2_EUNSUPPORTED for 4096-bit keys.
  *  - PC2_ERANGE if one CTA's share of scratch for this key would exceed the
- *    array (it does not for any supported key size); the element count itself
+ *    array (it does not for the key sizes above); the element count itself
  *    is not limited.  The key's host-side constants are built and cached in
  *    host memory on its first decryption, as for pc2_decrypt.
  *  - PC2_EKEY for a public key; PC2_EINVAL for null pointers. */
