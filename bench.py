@@ -33,11 +33,12 @@ SEED, STREAM = 0xB300, 1
 METRIC = "Paillier enc/dec per s @2048-bit"
 UNIT = "Paillier enc+dec ops/s"
 # DRAM bytes (read + write) per element of k_enc_crt<64,1> from one ncu capture
-# of this build (2^17 elements: 10.77 GB + 4.27 GB; profiles/k_enc_crt_2048_small_full.md),
-# scaled to a launch by the elements it processes; None once the kernel changes.
+# of this build (2^17 elements: 10.77 GB + 4.27 GB), scaled to a launch by the
+# elements it processes; None once the kernel changes.
 ENC_DRAM_BYTES_PER_ELEM = 114776
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
-IMAD_PER_CLK_SM = 64   # 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
+IMAD_PER_CLK_SM = 64   # nominal 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
+CPU_PER_GROUP = 4      # CPU sample: 16 x 4 encryptions, 16-group products, 4 decryptions per step
 
 
 def _peaks():
@@ -58,10 +59,11 @@ def _oracle_sample(args):
     return c
 
 
-def _cpu_reference(steps: int, warmup: int, per_group: int = 4):
+def _cpu_reference(steps: int, warmup: int, per_group: int = CPU_PER_GROUP, workers: int | None = None):
     """Time the oracle (as it stands) on the host cores: each step encrypts
     16 x per_group plaintexts, multiplies the 16 groups, decrypts per_group
-    aggregates.  Returns (ops/s, cores, sample description, seconds/step)."""
+    aggregates, in a process pool of `workers` (default: every core).
+    Returns (ops/s, cores, sample description, seconds/step)."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
@@ -71,7 +73,7 @@ def _cpu_reference(steps: int, warmup: int, per_group: int = 4):
     p, q = W.primes(NBITS, 2026)
     ko = O.derive_key(p, q)
     m = W.plaintexts_u64(GROUPS * per_group, seed=7)
-    cores = os.cpu_count() or 1
+    cores = workers or os.cpu_count() or 1
     work = [(p, q, [int(m[g * per_group + i])], [g * (N_PLAIN // GROUPS) + i], SEED, STREAM)
             for g in range(GROUPS) for i in range(per_group)]
     times = []
@@ -88,9 +90,29 @@ def _cpu_reference(steps: int, warmup: int, per_group: int = 4):
                 times.append(t1 - t0)
     per = statistics.mean(times)
     ops = GROUPS * per_group + per_group
-    sample = "%d encryptions + %d-group products + %d decryptions per step (of the 2^20 workload), process pool" % (
-        GROUPS * per_group, GROUPS, per_group)
+    sample = ("%d encryptions + %d-group products + %d decryptions per step (of the 2^20 workload), mean of %d "
+              "steps, process pool of %d" % (GROUPS * per_group, GROUPS, per_group, steps, cores))
     return ops / per, cores, sample, per
+
+
+def _python_pow_reference(count: int = 8):
+    """Secondary CPU reference, one thread: Eq. (itq1) and Sec. III-C with
+    CPython's built-in three-argument pow on the same key and draws."""
+    from oracle import paillier as O
+    from paper_2601_14980_b300 import workloads as W
+
+    p, q = W.primes(NBITS, 2026)
+    ko = O.derive_key(p, q)
+    m = [int(x) for x in W.plaintexts_u64(count, seed=7)]
+    r = [O.r_of(ko, SEED, STREAM, e) for e in range(count)]
+    t0 = time.perf_counter()
+    c = [(1 + mi * ko.n) * pow(ri, ko.n, ko.n2) % ko.n2 for mi, ri in zip(m, r)]
+    t1 = time.perf_counter()
+    d = [(pow(ci, ko.lam, ko.n2) - 1) // ko.n * ko.mu % ko.n for ci in c]
+    t2 = time.perf_counter()
+    assert d == m
+    return {"enc_per_s": count / (t1 - t0), "dec_per_s": count / (t2 - t1), "threads": 1,
+            "sample": "%d encryptions and decryptions at 2048-bit n, CPython pow" % count}
 
 
 def _dec_worker(args):
@@ -150,6 +172,50 @@ def _admm_setup(L, sizes):
     return np.concatenate(alpha), np.concatenate(Bbar)
 
 
+def _mse_gap_bound(ctx, sizes, Bbar, xs, zs, vs, x_plain, x0, zmin: float, log2_scale: int):
+    """Bound on |MSE_priv - MSE_plain| after len(xs) private rounds: per round
+    and element, the quantization errors carried through the local update,
+    eps_i = 1/(2 S^2) + sum_j (|w~_j| / (2S) + |Bbar_ij| / S) + ulp(x_i)
+    with w~ the dequantized z - v the round started from; with G_0 = 0,
+    G_t = 2 G_{t-1} + ||eps_t||, Delta_T = G_{T-1} + ||eps_T|| bounds
+    ||x_priv - x_plain|| (the soft threshold and its complement are firmly
+    nonexpansive, ||Bbar_k|| <= 1), and the MSE gap is at most
+    (2 ||x_plain - x0|| Delta_T + Delta_T^2) / N.  Tensors on the device."""
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    S = float(2 ** log2_scale)
+    N = int(sum(sizes))
+    off = [0]
+    for n in sizes:
+        off.append(off[-1] + int(n))
+    rowabs = torch.empty(N, dtype=torch.float64, device=Bbar.device)
+    b0 = 0
+    for k, n in enumerate(sizes):
+        rowabs[off[k]:off[k + 1]] = Bbar[b0:b0 + n * n].view(n, n).abs().sum(dim=1) / S
+        b0 += n * n
+    G, dT = 0.0, 0.0
+    zp = torch.zeros(N, dtype=torch.float64, device=Bbar.device)
+    vp = torch.zeros_like(zp)
+    for t in range(len(xs)):
+        zq = pc2.quantize(ctx, zp, zmin, -zmin, log2_scale, 2).double()
+        vq = pc2.quantize(ctx, vp, zmin, -zmin, log2_scale, 2, negate=True).double()
+        wt = ((zq + vq) / S + 2 * zmin).abs() / (2 * S)
+        eps = torch.empty(N, dtype=torch.float64, device=Bbar.device)
+        for k in range(len(sizes)):
+            eps[off[k]:off[k + 1]] = wt[off[k]:off[k + 1]].sum()
+        x = xs[t]
+        ulp = torch.nextafter(x.abs(), torch.full_like(x, float("inf"))) - x.abs()
+        eps += 0.5 / S ** 2 + rowabs + ulp
+        e = float(torch.linalg.norm(eps))
+        dT = G + e
+        G = 2 * G + e
+        zp, vp = zs[t], vs[t]
+    gap = (2 * float(torch.linalg.norm(x_plain - x0)) * dT + dT ** 2) / N
+    return dT, gap
+
+
 def run_admm(dev, rounds: int = 5):
     """Seconds per ADMM iteration on the small LASSO workload (1024-bit n,
     4 nodes): batched rounds (one graph per round) vs the per-node path."""
@@ -179,8 +245,14 @@ def run_admm(dev, rounds: int = 5):
         b.synchronize()
         out[name] = a.elapsed_time(b) / 1e3 / rounds
         if name == "batched":
-            x = adm.get()[0].cpu().numpy()
-            out["mse"] = float(np.mean((x - L.x0) ** 2))
+            # the same rounds again, one at a time, keeping the iterates for the bound
+            adm.reset()
+            xs, zs, vs = [], [], []
+            for _ in range(rounds):
+                adm.round(1)
+                x, z, v, _ = adm.get()
+                xs.append(x.clone()), zs.append(z.clone()), vs.append(v.clone())
+            out["mse"] = float(np.mean((xs[-1].cpu().numpy() - L.x0) ** 2))
             adm.reset()
             torch.cuda.synchronize()
             a.record(st)
@@ -188,12 +260,17 @@ def run_admm(dev, rounds: int = 5):
             b.record(st)
             b.synchronize()
             out["plain_dis_admm"] = a.elapsed_time(b) / 1e3 / rounds
-            out["mse_plain"] = float(np.mean((adm.get()[0].cpu().numpy() - L.x0) ** 2))
+            xp = adm.get()[0].clone()
+            out["mse_plain"] = float(np.mean((xp.cpu().numpy() - L.x0) ** 2))
+            x0 = torch.from_numpy(L.x0).to(dev)
+            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, dB, xs, zs, vs, xp, x0, -8.0, 24)
         adm.close()
     return {"workload": "lasso_small: A 128x256, 4 edge nodes, 1024-bit n, %d rounds" % rounds,
             "s_per_iter_batched": out["batched"], "s_per_iter_per_node": out["per_node"],
             "batched_speedup": out["per_node"] / out["batched"], "s_per_iter_plaintext_dis_admm": out["plain_dis_admm"],
-            "mse_private": out["mse"], "mse_plaintext": out["mse_plain"]}
+            "mse_private": out["mse"], "mse_plaintext": out["mse_plain"],
+            "mse_gap": abs(out["mse"] - out["mse_plain"]), "mse_bound": out["bound"], "delta_T": out["delta_T"],
+            "within_bound": abs(out["mse"] - out["mse_plain"]) <= out["bound"]}
 
 
 def run_admm_full(dev, rounds: int = 2):
@@ -223,20 +300,37 @@ def run_admm_full(dev, rounds: int = 2):
     out = {}
     for name, per_node in (("batched", False), ("per_node", True)):
         adm = pc2.Admm(ctx, key, sizes, alpha, Bbar, lam, rho, -8.0, 8.0, 24, 77, per_node=per_node)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        adm.round(rounds)
-        b.record(st)
-        b.synchronize()
-        out[name] = a.elapsed_time(b) / 1e3 / rounds
+        ms = 0.0
+        xs, zs, vs = [], [], []
+        for _ in range(rounds):          # round 1 eager, then the captured graph
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            adm.round(1)
+            b.record(st)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            if name == "batched":
+                x, z, v, _ = adm.get()
+                xs.append(x.clone()), zs.append(z.clone()), vs.append(v.clone())
+        out[name] = ms / 1e3 / rounds
         if name == "batched":
-            out["mse"] = float(np.mean((adm.get()[0].cpu().numpy() - x0) ** 2))
+            x0d = torch.from_numpy(x0).to(dev)
+            out["mse"] = float(((xs[-1] - x0d) ** 2).mean())
             out["matvec"] = adm.info()
+            adm.reset()
+            adm.round_plain(rounds)
+            xp = adm.get()[0].clone()
+            out["mse_plain"] = float(((xp - x0d) ** 2).mean())
+            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, Bbar, xs, zs, vs, xp, x0d, -8.0, 24)
+            del xs, zs, vs
         adm.close()
     return {"workload": "lasso_large: N=65536 (256x256, 5%% DCT nonzeros), 16 edge nodes, A %dx%d, 3072-bit n, "
                         "%d rounds" % (len(y), len(x0), rounds),
             "s_per_iter_batched": out["batched"], "s_per_iter_per_node": out["per_node"],
             "batched_speedup": out["per_node"] / out["batched"], "mse_after_rounds": out["mse"],
+            "mse_plaintext_after_rounds": out["mse_plain"], "mse_gap": abs(out["mse"] - out["mse_plain"]),
+            "mse_bound": out["bound"], "delta_T": out["delta_T"],
+            "within_bound": abs(out["mse"] - out["mse_plain"]) <= out["bound"],
             "matvec": out["matvec"], "status": ctx.status()}
 
 
@@ -491,6 +585,32 @@ def run_hbm(dev, n: int = 1 << 27, n_dec: int = 1 << 24, reps: int = 5):
     return {"peak_gb_s": peak, "peak_note": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)", "steps": out}
 
 
+def run_probe(dev) -> dict:
+    """Measured rates of the 32-bit multiplies on this GPU (pc2_probe_mul):
+    mad.lo, mad.hi, mad.wide (a whole 32x32->64 product), a product as
+    mad.lo + mad.hi, and the carry-chained rows of a 64-limb Montgomery
+    product at the encryption kernel's occupancy (3 CTAs of 128 per SM).
+    Per SM and clock from clock64 inside the loops; per second from CUDA
+    events around each launch (after one untimed warm-up launch)."""
+    from paper_2601_14980_b300 import pc2
+
+    kinds = [("mad_lo", pc2.PROBE_LO, 8, 40000), ("mad_hi", pc2.PROBE_HI, 8, 20000),
+             ("mad_wide", pc2.PROBE_WIDE, 8, 20000), ("lo_hi_product", pc2.PROBE_LOHI, 8, 15000),
+             ("cios_row_64_limbs", pc2.PROBE_ROW, 3, 600)]
+    out = {}
+    clk = Clocks(dev)
+    for name, kind, bps, iters in kinds:
+        pc2.probe_mul(dev, kind, bps, max(1, iters // 10))
+        r = pc2.probe_mul(dev, kind, bps, iters)
+        out[name] = {"per_clk_per_sm": r["ops"] / (r["cycles"] * r["sms"]), "per_s": r["ops"] / (r["ms"] / 1e3),
+                     "ms": r["ms"], "ctas_per_sm": bps, "sm_mhz": r["cycles"] / (r["ms"] * 1e3)}
+    out["clocks"] = clk.stop()
+    wide, lohi = out["mad_wide"]["per_s"], out["lo_hi_product"]["per_s"]
+    out["product_peak_per_s"] = max(wide, lohi)
+    out["product_peak_kind"] = "mad_wide" if wide >= lohi else "lo_hi_product"
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -513,8 +633,11 @@ def run_gpu(args):
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, per = _cpu_reference(steps=1, warmup=0)
-        cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v, cores, sample, per = _cpu_reference(steps=3, warmup=1)
+        v1, _, sample1, _ = _cpu_reference(steps=1, warmup=0, per_group=1, workers=1)
+        cpu_base = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                    "single_thread": {"value": v1, "sample": sample1},
+                    "python_pow": _python_pow_reference()}
 
     global N_PLAIN, GROUPS
     N_PLAIN, GROUPS = args.plaintexts, args.groups
@@ -584,20 +707,67 @@ def run_gpu(args):
     ops = (N_PLAIN + per_group) * world
     value = ops / (ms / 1e3)
 
-    # roofline of the dominant kernel (encryption): algorithmic IMADs / time
+    # decryption of the whole batch (all 2^20 ciphertexts), outside the step
+    dec_full_ms = None
+    if rank == 0:
+        dec_full = torch.empty(pc2.tiled_words(N_PLAIN, key.limbs), dtype=torch.int32, device=dev)
+        reps = []
+        for _ in range(2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            pc2.decrypt(ctx, key, ct, N_PLAIN, out=dec_full)
+            b.record(st)
+            b.synchronize()
+            reps.append(a.elapsed_time(b))
+        dec_full_ms = statistics.mean(reps)
+        del dec_full
+
+    # roofline of the dominant kernel (encryption): algorithmic 32x32->64
+    # word products / time, against the measured product rate of the multiplier
     mm, mmh, lb = key.cost(ctx, pc2.COST_ENCRYPT)
     imad_per_elem = key.imads(ctx, pc2.COST_ENCRYPT)
+    prod_enc = key.products(ctx, pc2.COST_ENCRYPT)
+    prod_dec = key.products(ctx, pc2.COST_DECRYPT)
+    prod_sum = GROUPS * (2 * L2 * L2 + L2)      # (groups - 1) products and the R^k fix-up, n^2 limbs
     enc_ms = statistics.mean(t_enc)
-    achieved = imad_per_elem * N_PLAIN / (enc_ms / 1e3) / 1e12
+    dec_ms = statistics.mean(t_dec)
+    sum_ms = statistics.mean(t_sum)
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2032.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12
+    nominal_imad = sms * IMAD_PER_CLK_SM * sm_max * 1e6 / 1e12
+    probe = None
+    if rank == 0 and not args.no_probe:
+        probe = run_probe(dev)
     dmm, _, dlb = key.cost(ctx, pc2.COST_DECRYPT)
-    dec_ms = statistics.mean(t_dec)
     if rank != 0:
         if dist: dist.destroy_process_group()
         return
+    ach_enc = prod_enc * N_PLAIN / (enc_ms / 1e3) / 1e12
+    fr = {}
+    if probe:
+        peak = probe["product_peak_per_s"] / 1e12
+        lohi = probe["lo_hi_product"]["per_s"] / 1e12
+        for name, prods, cnt, t in (("k_enc_crt", prod_enc, N_PLAIN, enc_ms), ("k_dec_crt (2^16 aggregates)", prod_dec,
+                                    per_group, dec_ms), ("k_dec_crt (2^20 ciphertexts)", prod_dec, N_PLAIN, dec_full_ms),
+                                    ("k_hom_sum", prod_sum, per_group, sum_ms)):
+            a = prods * cnt / (t / 1e3) / 1e12
+            fr[name] = {"achieved_tprod_s": a, "frac_of_measured_peak": a / peak, "frac_of_lo_hi_rate": a / lohi}
+        roof = {"bound": "alu", "kernel": "k_enc_crt", "achieved": ach_enc, "peak": peak,
+                "unit": "T word products/s (32x32->64)", "frac": ach_enc / peak,
+                "peak_note": "measured: pc2_probe_mul %s rate (of measured), the fastest way this GPU forms a "
+                             "32x32->64 product; %.0f MHz effective" % (probe["product_peak_kind"],
+                                                                        probe[probe["product_peak_kind"]]["sm_mhz"]),
+                "nominal": {"peak_timad_s": nominal_imad, "achieved_timad_s": imad_per_elem * N_PLAIN / (enc_ms / 1e3) / 1e12,
+                            "note": "%d SMs x %d IMAD/clk x %.0f MHz, hi and lo halves counted as two IMADs" % (
+                                sms, IMAD_PER_CLK_SM, sm_max)}}
+    else:
+        a = imad_per_elem * N_PLAIN / (enc_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_enc_crt", "achieved": a, "peak": nominal_imad, "unit": "TIMAD/s",
+                "frac": a / nominal_imad, "peak_note": "nominal (probe skipped): %d SMs x %d IMAD/clk x %.0f MHz" % (
+                    sms, IMAD_PER_CLK_SM, sm_max)}
+    roof["traffic"] = ENC_DRAM_BYTES_PER_ELEM * N_PLAIN if ENC_DRAM_BYTES_PER_ELEM else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -605,13 +775,16 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n_bits": NBITS, "plaintexts_per_gpu": N_PLAIN, "groups": GROUPS,
                    "encrypt_path": "key-owner CRT (mod p^2, q^2)", "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "dp%d (independent shards)" % world},
-        "detail": {"encrypt_ms": enc_ms, "hom_sum_ms": statistics.mean(t_sum), "decrypt_ms": dec_ms,
+        "detail": {"encrypt_ms": enc_ms, "hom_sum_ms": sum_ms, "decrypt_ms": dec_ms,
                    "enc_per_s": N_PLAIN / (enc_ms / 1e3), "dec_per_s": per_group / (dec_ms / 1e3),
+                   "decrypt_all_2p20_ms": dec_full_ms,
+                   "dec_per_s_all_2p20": N_PLAIN / (dec_full_ms / 1e3) if dec_full_ms else None,
                    "enc_montmuls_per_elem": mm, "enc_half_width_montmuls_per_elem": mmh,
-                   "dec_montmuls_per_elem": dmm, "montmul_limbs": lb, "enc_imads_per_elem": imad_per_elem},
-        "roofline": {"bound": "alu", "kernel": "k_enc_crt", "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
-                     "frac": achieved / peak, "traffic": ENC_DRAM_BYTES_PER_ELEM * N_PLAIN if ENC_DRAM_BYTES_PER_ELEM else None,
-                     "peak_note": "%d SMs x %d IMAD/clk x %.0f MHz (unit count x max SM clock)" % (sms, IMAD_PER_CLK_SM, sm_max)},
+                   "dec_montmuls_per_elem": dmm, "montmul_limbs": lb, "enc_imads_per_elem": imad_per_elem,
+                   "enc_products_per_elem": prod_enc, "dec_products_per_elem": prod_dec,
+                   "hom_sum_products_per_elem": prod_sum, "fractions": fr},
+        "multiplier_probe": probe,
+        "roofline": roof,
         "e2e": {"value": ops / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(m_pinned.numel() * 8),
                 "d2h_bytes_per_step": int(dec_host.numel() * 4)},
         "gpu_launches": 3 * args.steps,
@@ -622,7 +795,7 @@ def run_gpu(args):
         "serve": None if args.no_serve else run_serve(dev),
         "table2": None if args.no_table2 else run_table2(dev),
         "hbm": None if args.no_hbm else run_hbm(dev, n=args.hbm_elems, n_dec=min(args.hbm_elems, 1 << 24)),
-        "admm_full": run_admm_full(dev) if args.admm_full else None,
+        "admm_full": None if args.no_admm_full else run_admm_full(dev),
     }
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
@@ -633,7 +806,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    v, cores, sample, per = _cpu_reference(steps=args.steps, warmup=args.warmup, per_group=1)
+    v, cores, sample, per = _cpu_reference(steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -658,7 +831,8 @@ def main():
     ap.add_argument("--no-table2", action="store_true", help="skip the Table II operations at 1024/2048/4096 bits")
     ap.add_argument("--no-hbm", action="store_true", help="skip the bandwidth of the memory-bound steps")
     ap.add_argument("--hbm-elems", type=int, default=1 << 27, help="vector length of the bandwidth section")
-    ap.add_argument("--admm-full", action="store_true", help="also time the full-scale 3072-bit ADMM (about 2 min)")
+    ap.add_argument("--no-admm-full", action="store_true", help="skip the full-scale 3072-bit ADMM (about 2 min)")
+    ap.add_argument("--no-probe", action="store_true", help="skip the multiplier probe (roofline on the nominal peak)")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
     ap.add_argument("--groups", type=int, default=GROUPS)

@@ -391,6 +391,33 @@ int pc2_server_wait(pc2_server* server, uint64_t ticket, double timeout_s, doubl
 /* Requests completed, steps launched, work items run, peak arena bytes in use. */
 int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, uint64_t* items, size_t* arena_peak);
 
+/* ---- integer-multiplier throughput probe ---------------------------- *
+ * A measurement aid (the paper has no counterpart): the modular
+ * exponentiations of Eq. (itq1) and Sec. III-C are bound by the 32-bit
+ * multiply pipe, and their roofline is quoted against the rate this probe
+ * measures on the device.  kind:
+ *   PC2_PROBE_LO    mad.lo.u32 (low half of a 32x32 product, plus an add)
+ *   PC2_PROBE_HI    mad.hi.u32 (high half)
+ *   PC2_PROBE_WIDE  mad.wide.u32 (a whole 32x32->64 product, plus a 64-bit add)
+ *   PC2_PROBE_LOHI  a 32x32->64 product as mad.lo + mad.hi
+ *   PC2_PROBE_ROW   the carry-chained rows of a 64-limb Montgomery product,
+ *                   the instruction pattern of the library's product core
+ * Launches blocks_per_sm x SMs CTAs of 128 threads (PC2_EINVAL when that
+ * many cannot all be resident, or iters < 1); every thread runs `iters`
+ * loop trips of independent accumulators.  Allocates its own small buffers
+ * (cudaMalloc) and synchronises the stream.
+ * Out (host): *ops = operations executed (multiplies of that kind; 32x32->64
+ * products for WIDE, LOHI and ROW); *ms = CUDA-event time of the launch on
+ * `stream`; *cycles = the longest CTA's clock64 cycles inside its loop;
+ * *sms = the device's SM count (may be NULL). */
+#define PC2_PROBE_LO 0
+#define PC2_PROBE_HI 1
+#define PC2_PROBE_WIDE 2
+#define PC2_PROBE_LOHI 3
+#define PC2_PROBE_ROW 4
+int pc2_probe_mul(int device, int kind, int blocks_per_sm, int iters, pc2_stream_t stream, double* ops, double* ms,
+                  double* cycles, int* sms);
+
 /* ---- decryption without device allocation ---------------------------- *
  * Not from the paper (it has no counterpart there): a variant of pc2_decrypt
  * for callers that may not allocate device memory -- a process held to a
@@ -406,8 +433,14 @@ int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, u
  *    Nothing in the array needs to start at zero: every word a call reads is
  *    written by that call first.
  *  - Runs on the calling thread's current device.  The FIRST call on each
- *    device looks up the array's device address (cudaGetSymbolAddress); make
- *    that first call before any stream capture.
+ *    device looks up the array's device address (cudaGetSymbolAddress).
+ *    With lazy module loading (the CUDA default) that lookup is also where
+ *    the runtime loads this code's module and maps the 64 MiB array on the
+ *    device, which can fail (PC2_ECUDA) or synchronise.  So make one warm-up
+ *    call (count = 1 is enough) at start-up, before the caller's memory
+ *    budget is carved and before any stream capture.
+ *  - The address is cached per device for the life of the process: do not
+ *    use this entry point across a cudaDeviceReset.
  *  - All calls share the one array: calls whose kernels overlap on a GPU
  *    (different streams, or different host threads) race and corrupt each
  *    other's results.  Order them on one stream.

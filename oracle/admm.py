@@ -309,3 +309,42 @@ def private_admm(setup: DisSetup, lam, rho, iters, qp: QParams, key: P.Key, seed
         tr.zhat.append(zhat)
         tr.vhat.append(vhat)
     return tr
+
+
+# ------------------------------------------------------------------ quantization error bound
+
+
+def round_error_bound(setup: DisSetup, qp: QParams, z_prev, v_prev, x_priv) -> np.ndarray:
+    """Per-element bound on |x_priv - x_plain| after one round from the same
+    (z, v): the quantization errors of Eq. (et21) (half a step of Gamma1 on
+    alpha, of Gamma2 on Bbar and on w = z - v) carried through the local
+    update of Eq. (sldo091), plus one rounding of x:
+    1/(2 S^2) + sum_j (|w~_j| / (2S) + |Bbar_ij| / S) + ulp(x_i)."""
+    S = qp.S
+    zq, vq = gamma2(z_prev, qp), gamma2(-np.asarray(v_prev), qp)
+    wt = (zq + vq) / S + 2 * qp.zmin
+    eps = np.empty(len(x_priv))
+    for k, (a0, a1) in enumerate(zip(setup.offsets[:-1], setup.offsets[1:])):
+        wsum = np.sum(np.abs(wt[a0:a1])) / (2 * S)
+        rows = np.sum(np.abs(setup.Bbar[k]), axis=1) / S
+        eps[a0:a1] = 0.5 / S ** 2 + wsum + rows + np.spacing(np.abs(x_priv[a0:a1]))
+    return eps
+
+
+def mse_gap_bound(setup: DisSetup, qp: QParams, xs, zs, vs, x_plain, x0) -> tuple[float, float]:
+    """(Delta_T, bound on |MSE_priv - MSE_plain|) after T = len(xs) rounds of
+    the private loop (iterates xs, zs, vs per round) against plaintext
+    Dis-ADMM ending at x_plain.  The soft threshold and its complement are
+    firmly nonexpansive and ||Bbar_k|| <= 1, so with G_0 = 0 and
+    G_t = 2 G_{t-1} + ||eps_t||: ||x_priv^T - x_plain^T|| <= G_{T-1} +
+    ||eps_T|| = Delta_T, and |MSE_priv - MSE_plain| <= (2 ||x_plain - x0||
+    Delta_T + Delta_T^2) / N."""
+    N = len(x0)
+    G, dT = 0.0, 0.0
+    zp, vp = np.zeros(N), np.zeros(N)
+    for t in range(len(xs)):
+        e = float(np.linalg.norm(round_error_bound(setup, qp, zp, vp, xs[t])))
+        dT = G + e
+        G = 2 * G + e
+        zp, vp = zs[t], vs[t]
+    return dT, (2 * float(np.linalg.norm(np.asarray(x_plain) - x0)) * dT + dT ** 2) / N

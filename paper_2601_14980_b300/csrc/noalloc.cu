@@ -10,9 +10,10 @@
 // For them pc2_decrypt_noalloc runs the same decryption kernel with its
 // scratch in a fixed array compiled into the library.
 //
-// The array below is a host-side stand-in in host code: its device address
-// is looked up once per device with cudaGetSymbolAddress and only that
-// address is handed to the kernel.
+// The array below lives in device memory (a file-scope __device__ array, one
+// copy per GPU that loads the library).  In host code its name is only a
+// handle, not a device address: host code looks the address up once per
+// device with cudaGetSymbolAddress and passes that address to the kernel.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,7 +34,9 @@ std::mutex g_mu;
 uint32_t* g_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device (looked up on
-// the first call for that device).
+// the first call for that device and cached for the life of the process; a
+// cudaDeviceReset invalidates it, so the entry point must not be used across
+// one).
 int scratch_address(int dev, uint32_t** out) {
   if (dev < 0 || dev >= kMaxDevices) return PC2_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);

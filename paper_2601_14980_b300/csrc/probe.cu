@@ -1,0 +1,169 @@
+// probe.cu -- throughput probe of the integer multiplier (pc2_probe_mul).
+//
+// The modular exponentiations are bound by the 32-bit multiply pipe, so
+// their roofline needs its measured rate on this GPU, not a nominal unit
+// count.  Each kernel below keeps several independent accumulators per
+// thread (enough instruction-level parallelism that latency is hidden at
+// full occupancy) and counts the operations it issues:
+//   LO    mad.lo.u32            low half of a 32x32 product, plus an add
+//   HI    mad.hi.u32            high half
+//   WIDE  mad.wide.u32          a whole 32x32->64 product plus a 64-bit add
+//   LOHI  mad.lo + mad.hi       a 32x32->64 product from two halves
+//   ROW   the carry-chained row of a 64-limb Montgomery product
+//         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc), the exact
+//         instruction pattern of the library's product core; one product per
+//         limb and row.
+// Cycles come from clock64 around the loop (max over CTAs), time from CUDA
+// events around the launch.
+#include <cuda_runtime.h>
+
+#include "../../include/pc2.h"
+#include "mont.cuh"
+
+namespace {
+
+constexpr int kProbeThreads = 128;
+constexpr int kIlp = 8;
+
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) k_probe(uint32_t seed, int iters, uint32_t* sink,
+                                                         long long* cycles) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t b = seed * 2654435761u + tid;
+  long long t0 = 0;
+  uint32_t fold = 0;
+  if constexpr (KIND == PC2_PROBE_ROW) {
+    uint32_t a[64], t[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      a[j] = b ^ (j * 0x9e3779b9u);
+      t[j] = j;
+    }
+    uint32_t c0 = 0, c1 = 0;
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll 1
+      for (int r = 0; r < 64; ++r) {
+        pc2::row_mac<64>(t, c0, c1, pc2::RegA<64>{a}, b + r);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 64; ++j) fold ^= t[j];
+    fold ^= c0 ^ c1;
+  } else if constexpr (KIND == PC2_PROBE_WIDE) {
+    uint64_t x[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) x[k] = b + k;
+    const uint32_t a = b | 1u;
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[k]) : "r"(a), "r"(b));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) fold ^= (uint32_t)x[k] ^ (uint32_t)(x[k] >> 32);
+  } else {
+    uint32_t x[kIlp], y[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+      x[k] = b + k;
+      y[k] = b ^ k;
+    }
+    const uint32_t a = b | 1u;
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+          if constexpr (KIND == PC2_PROBE_LO || KIND == PC2_PROBE_LOHI)
+            asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(x[k]) : "r"(a), "r"(b));
+          if constexpr (KIND == PC2_PROBE_HI || KIND == PC2_PROBE_LOHI)
+            asm volatile("mad.hi.u32 %0, %1, %2, %0;" : "+r"(y[k]) : "r"(a), "r"(b));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) fold ^= x[k] ^ y[k];
+  }
+  const long long t1 = clock64();
+  __syncthreads();
+  if (fold == 0x12345678u) sink[tid] = fold;  // keeps the work observable
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+template <int KIND>
+double ops_per_thread(int iters) {
+  if constexpr (KIND == PC2_PROBE_ROW) return (double)iters * 64.0 * 64.0;
+  else return (double)iters * 16.0 * kIlp;
+}
+
+template <int KIND>
+int run(int sms, int blocks_per_sm, int iters, cudaStream_t st, double* ops, double* ms, double* cycles) {
+  auto kern = k_probe<KIND>;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kProbeThreads, 0) != cudaSuccess) return PC2_ECUDA;
+  if (blocks_per_sm < 1 || blocks_per_sm > per) return PC2_EINVAL;  // every CTA must be resident
+  const int grid = blocks_per_sm * sms;
+  uint32_t* sink = nullptr;
+  long long* cyc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PC2_OK;
+  if (cudaMalloc(&sink, (size_t)grid * kProbeThreads * 4) != cudaSuccess ||
+      cudaMalloc(&cyc, (size_t)grid * sizeof(long long)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    rc = PC2_ENOMEM;
+  } else {
+    cudaEventRecord(e0, st);
+    kern<<<grid, kProbeThreads, 0, st>>>(0x5eedu, iters, sink, cyc);
+    cudaEventRecord(e1, st);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = PC2_ECUDA;
+    } else {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      long long* h = new long long[grid];
+      if (cudaMemcpy(h, cyc, (size_t)grid * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess) rc = PC2_ECUDA;
+      long long mx = 0;
+      for (int i = 0; i < grid; ++i) mx = h[i] > mx ? h[i] : mx;
+      delete[] h;
+      *ops = ops_per_thread<KIND>(iters) * (double)grid * kProbeThreads;
+      *ms = t;
+      *cycles = (double)mx;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (sink) cudaFree(sink);
+  if (cyc) cudaFree(cyc);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int pc2_probe_mul(int device, int kind, int blocks_per_sm, int iters, pc2_stream_t stream, double* ops,
+                             double* ms, double* cycles, int* sms_out) {
+  if (!ops || !ms || !cycles || iters < 1) return PC2_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return PC2_ECUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return PC2_ECUDA;
+  if (sms_out) *sms_out = sms;
+  const cudaStream_t st = (cudaStream_t)stream;
+  switch (kind) {
+    case PC2_PROBE_LO: return run<PC2_PROBE_LO>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_HI: return run<PC2_PROBE_HI>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_WIDE: return run<PC2_PROBE_WIDE>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_LOHI: return run<PC2_PROBE_LOHI>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_ROW: return run<PC2_PROBE_ROW>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    default: return PC2_EINVAL;
+  }
+}

@@ -199,6 +199,14 @@ class Key:
         _check(_key_cost(ctx.h, self.h, op, ctypes.byref(mm), ctypes.byref(mh), ctypes.byref(lb)), "pc2_key_cost")
         return mm.value, mh.value, lb.value
 
+    def products(self, ctx: Context, op: int) -> int:
+        """Algorithmic 32x32->64 word products per element of one op's powers:
+        a Montgomery product of L limbs takes 2 L^2 + L (the L^2 limb products
+        of a*b and of m*N, and L quotient words)."""
+        mm, mh, lb = self.cost(ctx, op)
+        h = lb // 2
+        return mm * (2 * lb * lb + lb) + mh * (2 * h * h + h)
+
     def imads(self, ctx: Context, op: int) -> int:
         """Algorithmic 32-bit multiply-adds per element of one op's powers: a
         Montgomery product of L limbs takes 4 L^2 + L (low and high halves of
@@ -657,3 +665,19 @@ def hom_matvec(ctx: Context, key: Key, alpha, s, K, n: int, kbits: int = 0, out=
     _check(_hom_matvec(ctx.h, key.h, _ptr(alpha), _ptr(s), _ptr(K), n, kbits, _ptr(out), _stream(stream)),
            "pc2_hom_matvec")
     return out
+
+
+# ------------------------------------------------------------------ multiplier probe
+PROBE_LO, PROBE_HI, PROBE_WIDE, PROBE_LOHI, PROBE_ROW = 0, 1, 2, 3, 4
+_probe_mul = _sig("pc2_probe_mul", [_i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(_i)])
+
+
+def probe_mul(device: int, kind: int, blocks_per_sm: int, iters: int, stream=None) -> dict:
+    """Throughput of one kind of 32-bit multiply (pc2_probe_mul): operations
+    executed, CUDA-event milliseconds, the longest CTA's cycles, SM count."""
+    ops, ms, cyc, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), _i()
+    _check(_probe_mul(device, kind, blocks_per_sm, iters, _stream(stream), ctypes.byref(ops), ctypes.byref(ms),
+                      ctypes.byref(cyc), ctypes.byref(sms)), "pc2_probe_mul")
+    return {"ops": ops.value, "ms": ms.value, "cycles": cyc.value, "sms": sms.value}

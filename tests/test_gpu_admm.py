@@ -81,6 +81,30 @@ def test_private_rounds_match_oracle_bit_exact(env):
         assert xh[i] == P.hom_matvec(ko, [ah[i]], s[o:o + 64], row)[0]
 
 
+def test_final_mse_within_quantization_bound(env):
+    """The small LASSO's five private GPU rounds end within the stated
+    quantization bound of plaintext Dis-ADMM (Theorem 1's errors carried
+    through the rounds): |MSE_priv - MSE_plain| <= bound, with the bound
+    computed from the GPU's own iterates and the plaintext path on the GPU."""
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=1)
+    st, kg, ko, adm = _make(env, L, 1024)
+    xs, zs, vs = [], [], []
+    for t in range(L.iters):
+        adm.round(1)
+        x, z, v, _ = adm.get()
+        xs.append(x.cpu().numpy()), zs.append(z.cpu().numpy()), vs.append(v.cpu().numpy())
+    adm.reset()
+    adm.round_plain(L.iters)
+    x_plain = adm.get()[0].cpu().numpy()
+    dT, bound = O.mse_gap_bound(st, QP, xs, zs, vs, x_plain, L.x0)
+    mse_priv = float(np.mean((xs[-1] - L.x0) ** 2))
+    mse_plain = float(np.mean((x_plain - L.x0) ** 2))
+    assert np.linalg.norm(xs[-1] - x_plain) <= dT
+    assert abs(mse_priv - mse_plain) <= bound
+    assert ctx.status() == 0
+
+
 def test_tiny_problem_against_real_encryption_oracle(env):
     torch, pc2, ctx = env
     L = W.lasso_small(seed=11, M=10, N=12, nnz=3, K=2)

@@ -141,20 +141,6 @@ def test_theorem1_private_equals_quantized():
         assert max(pr.D[t]) < key.n
 
 
-def round_error_bound(st, qp, z_prev, v_prev, x_priv):
-    """Per-round bound on |x_priv - x_plain| for the same (z, v) input:
-    1/(2 S^2) + sum_j (|w~_j| / (2S) + |Bbar_ij| / S) + one rounding."""
-    S = qp.S
-    zq, vq = O.gamma2(z_prev, qp), O.gamma2(-v_prev, qp)
-    wt = (zq + vq) / S + 2 * qp.zmin
-    eps = np.empty(len(x_priv))
-    for k, (a0, a1) in enumerate(zip(st.offsets[:-1], st.offsets[1:])):
-        for i in range(a1 - a0):
-            eps[a0 + i] = (0.5 / S ** 2 + np.sum(np.abs(wt[a0:a1]) / (2 * S) + np.abs(st.Bbar[k][i]) / S)
-                           + np.spacing(abs(x_priv[a0 + i])))
-    return eps
-
-
 def test_quantization_error_bound_and_mse():
     L, st = _setup_tiny(seed=12, N=24, K=3, M=16)
     qp = O.QParams(zmin=-8.0, zmax=8.0, log2_scale=24)
@@ -166,13 +152,13 @@ def test_quantization_error_bound_and_mse():
         x, _, _ = O.dis_admm(st, 0.01, 1.0, t)
         xs.append(x)
     # round 1: same (z, v) = 0 input
-    eps1 = round_error_bound(st, qp, np.zeros(24), np.zeros(24), qz.x[0])
+    eps1 = O.round_error_bound(st, qp, np.zeros(24), np.zeros(24), qz.x[0])
     assert np.all(np.abs(qz.x[0] - xs[0]) <= eps1 + 1e-14)
     # whole run: G_t <= 2 G_{t-1} + ||eps_t||, ||x_priv^T - x_plain^T|| <= G_{T-1} + ||eps_T||
     G = 0.0
     zp, vp = np.zeros(24), np.zeros(24)
     for t in range(T):
-        e = np.linalg.norm(round_error_bound(st, qp, zp, vp, qz.x[t]))
+        e = np.linalg.norm(O.round_error_bound(st, qp, zp, vp, qz.x[t]))
         bound_t = G + e
         assert np.linalg.norm(qz.x[t] - xs[t]) <= bound_t + 1e-12
         G = 2 * G + e
@@ -181,6 +167,8 @@ def test_quantization_error_bound_and_mse():
     mse_priv = np.mean((qz.x[-1] - L.x0) ** 2)
     mse_plain = np.mean((xs[-1] - L.x0) ** 2)
     assert abs(mse_priv - mse_plain) <= (2 * np.linalg.norm(xs[-1] - L.x0) * dT + dT ** 2) / 24
+    d2, mb = O.mse_gap_bound(st, qp, qz.x, qz.z, qz.v, xs[-1], L.x0)
+    assert abs(d2 + 1e-12 - dT) <= 1e-15 and abs(mse_priv - mse_plain) <= mb
 
 
 def test_diag_setup_is_the_orthonormal_closed_form():

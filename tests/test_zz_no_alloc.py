@@ -23,7 +23,9 @@ def _fn():
     return f
 
 
-@pytest.mark.parametrize("nbits,count", [(1024, 1000), (2048, 20000)])
+# 3072 bits: two lanes per element, and 5000 elements exceed what the cut grid
+# holds in one pass (58 CTAs x 64 elements), so the persistent loop runs.
+@pytest.mark.parametrize("nbits,count", [(512, 1000), (1024, 1000), (2048, 20000), (3072, 5000)])
 def test_decrypt_noalloc_matches_decrypt_twice(nbits, count):
     import torch
 
