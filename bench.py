@@ -172,45 +172,53 @@ def _admm_setup(L, sizes):
     return np.concatenate(alpha), np.concatenate(Bbar)
 
 
-def _mse_gap_bound(ctx, sizes, Bbar, xs, zs, vs, x_plain, x0, zmin: float, log2_scale: int):
-    """Bound on |MSE_priv - MSE_plain| after len(xs) private rounds: per round
-    and element, the quantization errors carried through the local update,
-    eps_i = 1/(2 S^2) + sum_j (|w~_j| / (2S) + |Bbar_ij| / S) + ulp(x_i)
-    with w~ the dequantized z - v the round started from; with G_0 = 0,
-    G_t = 2 G_{t-1} + ||eps_t||, Delta_T = G_{T-1} + ||eps_T|| bounds
-    ||x_priv - x_plain|| (the soft threshold and its complement are firmly
-    nonexpansive, ||Bbar_k|| <= 1), and the MSE gap is at most
-    (2 ||x_plain - x0|| Delta_T + Delta_T^2) / N.  Tensors on the device."""
+def _mse_gap_bound(ctx, sizes, alpha, Bbar, xs, zs, vs, x_plain, x0, zmin: float, log2_scale: int):
+    """Bound on |MSE_priv - MSE_plain| after len(xs) private rounds.  Scaled
+    ADMM is Douglas-Rachford on psi = z + v with a firmly nonexpansive
+    operator, so the per-round errors of x add up at most linearly:
+    Delta_T = sum_t ||eps_t|| with, per element, the quantization errors
+    carried through the local update, 1/(2 S^2) + sum_j (|w~_j| / (2S) +
+    |Bbar_ij| / S), one rounding of x, three ulps of |v| + |x| per run in the
+    z/v updates, and the plaintext matvec's dot-product error; then the MSE
+    gap is at most (2 ||x_plain - x0|| Delta_T + Delta_T^2) / N.  Tensors on
+    the device."""
     import torch
 
     from paper_2601_14980_b300 import pc2
 
     S = float(2 ** log2_scale)
+    u = 2.0 ** -53
     N = int(sum(sizes))
     off = [0]
     for n in sizes:
         off.append(off[-1] + int(n))
-    rowabs = torch.empty(N, dtype=torch.float64, device=Bbar.device)
-    b0 = 0
-    for k, n in enumerate(sizes):
-        rowabs[off[k]:off[k + 1]] = Bbar[b0:b0 + n * n].view(n, n).abs().sum(dim=1) / S
+    blocks, b0 = [], 0
+    for n in sizes:
+        blocks.append(Bbar[b0:b0 + n * n].view(n, n).abs())
         b0 += n * n
-    G, dT = 0.0, 0.0
+    rowabs = torch.cat([b.sum(dim=1) for b in blocks]) / S
+    inf = torch.tensor(float("inf"), dtype=torch.float64, device=Bbar.device)
+
+    def ulp(a):
+        a = a.abs()
+        return torch.nextafter(a, inf) - a
+
+    dT = 0.0
     zp = torch.zeros(N, dtype=torch.float64, device=Bbar.device)
     vp = torch.zeros_like(zp)
     for t in range(len(xs)):
         zq = pc2.quantize(ctx, zp, zmin, -zmin, log2_scale, 2).double()
         vq = pc2.quantize(ctx, vp, zmin, -zmin, log2_scale, 2, negate=True).double()
-        wt = ((zq + vq) / S + 2 * zmin).abs() / (2 * S)
+        wt = ((zq + vq) / S + 2 * zmin).abs()
         eps = torch.empty(N, dtype=torch.float64, device=Bbar.device)
         for k in range(len(sizes)):
-            eps[off[k]:off[k + 1]] = wt[off[k]:off[k + 1]].sum()
+            a0, a1 = off[k], off[k + 1]
+            n = a1 - a0 + 1
+            gam = n * u / (1 - n * u)
+            eps[a0:a1] = wt[a0:a1].sum() / (2 * S) + gam * (alpha[a0:a1].abs() + blocks[k] @ (wt[a0:a1] + dT))
         x = xs[t]
-        ulp = torch.nextafter(x.abs(), torch.full_like(x, float("inf"))) - x.abs()
-        eps += 0.5 / S ** 2 + rowabs + ulp
-        e = float(torch.linalg.norm(eps))
-        dT = G + e
-        G = 2 * G + e
+        eps += 0.5 / S ** 2 + rowabs + ulp(x) + 6 * ulp(vp.abs() + x.abs())
+        dT += float(torch.linalg.norm(eps))
         zp, vp = zs[t], vs[t]
     gap = (2 * float(torch.linalg.norm(x_plain - x0)) * dT + dT ** 2) / N
     return dT, gap
@@ -263,7 +271,7 @@ def run_admm(dev, rounds: int = 5):
             xp = adm.get()[0].clone()
             out["mse_plain"] = float(np.mean((xp.cpu().numpy() - L.x0) ** 2))
             x0 = torch.from_numpy(L.x0).to(dev)
-            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, dB, xs, zs, vs, xp, x0, -8.0, 24)
+            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, da, dB, xs, zs, vs, xp, x0, -8.0, 24)
         adm.close()
     return {"workload": "lasso_small: A 128x256, 4 edge nodes, 1024-bit n, %d rounds" % rounds,
             "s_per_iter_batched": out["batched"], "s_per_iter_per_node": out["per_node"],
@@ -321,7 +329,7 @@ def run_admm_full(dev, rounds: int = 2):
             adm.round_plain(rounds)
             xp = adm.get()[0].clone()
             out["mse_plain"] = float(((xp - x0d) ** 2).mean())
-            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, Bbar, xs, zs, vs, xp, x0d, -8.0, 24)
+            out["delta_T"], out["bound"] = _mse_gap_bound(ctx, sizes, alpha, Bbar, xs, zs, vs, xp, x0d, -8.0, 24)
             del xs, zs, vs
         adm.close()
     return {"workload": "lasso_large: N=65536 (256x256, 5%% DCT nonzeros), 16 edge nodes, A %dx%d, 3072-bit n, "
@@ -467,6 +475,47 @@ PAPER_TABLE2_RTX4060 = {
     2048: {"modmult": 1544.13e3, "modexp": 31080.16, "ep": 65662.72},
     4096: {"modmult": 1414.34e3, "modexp": 26594.01, "ep": 50053.47},
 }
+
+
+def run_tc_mont(dev, count: int = 1 << 20, nsq: int = 64, reps: int = 3):
+    """The tensor-core experiment: nsq Montgomery squarings of `count`
+    elements mod N = p^2 (2048 bits) of the benchmark's key, with the
+    reduction's contractions on tcgen05 (bf16 digits) vs the integer-pipe
+    CIOS product.  Inputs resident in device memory, CUDA events, mean of
+    `reps` after one warm-up; both results compared word for word."""
+    import torch
+
+    from paper_2601_14980_b300 import pc2
+
+    ctx = pc2.Context(dev)
+    p = pc2.Key.generate(NBITS, 2026).export()["p"]
+    N = p * p
+    g = torch.Generator(device=dev).manual_seed(9)
+    canon = torch.randint(-(1 << 31), 1 << 31, (count, 64), generator=g, dtype=torch.int64, device=dev)
+    canon[:, 63] = torch.randint(0, (N >> 2016) - 1, (count,), generator=g, device=dev)   # x < N
+    x = pc2.pack(ctx, canon.to(torch.int32).reshape(-1), count, 64)
+    st = torch.cuda.current_stream()
+    out, res = {}, {}
+    for name, eng in (("imad_cios", pc2.ENGINE_IMAD), ("tensor_core", pc2.ENGINE_TC)):
+        y = pc2.empty_tiled(count, 64)
+        pc2.mont_sqr(ctx, N, x, count, nsq, eng, out=y)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            pc2.mont_sqr(ctx, N, x, count, nsq, eng, out=y)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.mean(ms)
+        prods = count * nsq * (2 * 64 * 64 + 64)
+        out[name] = {"ms": t, "squarings_per_s": count * nsq / (t / 1e3), "t_word_products_per_s": prods / t / 1e9}
+        res[name] = y
+    same = bool(torch.equal(pc2.unpack(ctx, res["imad_cios"], count, 64), pc2.unpack(ctx, res["tensor_core"], count, 64)))
+    return {"workload": "%d elements x %d Montgomery squarings mod p^2 (2048 bits)" % (count, nsq), "engines": out,
+            "tc_over_imad": out["imad_cios"]["ms"] / out["tensor_core"]["ms"], "bit_identical": same,
+            "status": ctx.status()}
 
 
 def run_table2(dev, count: int = 9000, trials: int = 10):
@@ -796,6 +845,7 @@ def run_gpu(args):
         "table2": None if args.no_table2 else run_table2(dev),
         "hbm": None if args.no_hbm else run_hbm(dev, n=args.hbm_elems, n_dec=min(args.hbm_elems, 1 << 24)),
         "admm_full": None if args.no_admm_full else run_admm_full(dev),
+        "tc_mont": None if args.no_tc else run_tc_mont(dev),
     }
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
@@ -833,12 +883,19 @@ def main():
     ap.add_argument("--hbm-elems", type=int, default=1 << 27, help="vector length of the bandwidth section")
     ap.add_argument("--no-admm-full", action="store_true", help="skip the full-scale 3072-bit ADMM (about 2 min)")
     ap.add_argument("--no-probe", action="store_true", help="skip the multiplier probe (roofline on the nominal peak)")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Montgomery experiment")
+    ap.add_argument("--tc-only", action="store_true", help="run only the tensor-core Montgomery experiment")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")
     ap.add_argument("--groups", type=int, default=GROUPS)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.tc_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"tc_mont": run_tc_mont(0)}))
     else:
         run_gpu(args)
 

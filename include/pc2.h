@@ -391,6 +391,28 @@ int pc2_server_wait(pc2_server* server, uint64_t ticket, double timeout_s, doubl
 /* Requests completed, steps launched, work items run, peak arena bytes in use. */
 int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, uint64_t* items, size_t* arena_peak);
 
+/* ---- Montgomery squarings on the tensor cores (an experiment) ------- *
+ * nsq Montgomery squarings of each element: y = x^(2^nsq) R^-(2^nsq - 1)
+ * mod N, R = 2^(32 limbs), the dominant operation of the fixed-exponent
+ * powers of Eq. (itq1) and Sec. III-C.  engine PC2_ENGINE_IMAD runs the
+ * library's CIOS product on the integer pipe; PC2_ENGINE_TC computes the
+ * product a a on the integer pipe and the reduction's two contractions with
+ * the fixed modulus, m = (T mod R) N' mod R and m N, as bf16 tcgen05.mma
+ * over 8-bit digits (the paper's recasting of big-integer products as
+ * low-bitwidth matrix operations, Alg. 2, done on B300's tensor cores).  Both
+ * give the same integers.
+ *  - h_n: N, `limbs` little-endian words in host memory, odd; limbs = 64
+ *    (2048-bit N) only (PC2_EUNSUPPORTED otherwise).
+ *  - d_x, d_y: device, tiled layout of `limbs` words per element, x < N
+ *    (not checked); d_y may equal d_x.
+ *  - Asynchronous on `stream`; a wait inside the tensor-core kernel that
+ *    runs out raises PC2_ST_TIMEOUT in the context's status word.
+ *  - PC2_EINVAL: null pointers, even N, nsq < 0, unknown engine. */
+#define PC2_ENGINE_IMAD 0
+#define PC2_ENGINE_TC 1
+int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const uint32_t* d_x, size_t count, int nsq, int engine,
+                 uint32_t* d_y, pc2_stream_t stream);
+
 /* ---- integer-multiplier throughput probe ---------------------------- *
  * A measurement aid (the paper has no counterpart): the modular
  * exponentiations of Eq. (itq1) and Sec. III-C are bound by the 32-bit

@@ -334,17 +334,34 @@ def round_error_bound(setup: DisSetup, qp: QParams, z_prev, v_prev, x_priv) -> n
 def mse_gap_bound(setup: DisSetup, qp: QParams, xs, zs, vs, x_plain, x0) -> tuple[float, float]:
     """(Delta_T, bound on |MSE_priv - MSE_plain|) after T = len(xs) rounds of
     the private loop (iterates xs, zs, vs per round) against plaintext
-    Dis-ADMM ending at x_plain.  The soft threshold and its complement are
-    firmly nonexpansive and ||Bbar_k|| <= 1, so with G_0 = 0 and
-    G_t = 2 G_{t-1} + ||eps_t||: ||x_priv^T - x_plain^T|| <= G_{T-1} +
-    ||eps_T|| = Delta_T, and |MSE_priv - MSE_plain| <= (2 ||x_plain - x0||
-    Delta_T + Delta_T^2) / N."""
+    Dis-ADMM ending at x_plain.
+
+    Scaled ADMM is Douglas-Rachford splitting on psi = z + v: with prox_f(u) =
+    alpha + Bbar u (Eq. (sldo091); Bbar symmetric with eigenvalues in (0, 1],
+    the proximal map of f(x) = sum_k ||y - A_k x_k||^2 / 2) and prox_g the soft
+    threshold of Eq. (ty32), x^t = prox_f(2 prox_g(psi^{t-1}) - psi^{t-1}) and
+    psi^t = T(psi^{t-1}) = x^t + v^{t-1}, with T firmly nonexpansive (the
+    approximate-ADMM convergence argument the paper cites).  The private round
+    computes x^t plus an error e_t bounded elementwise by round_error_bound,
+    so ||psi_priv^t - psi^t|| <= sum_{s<=t} ||e_s|| and ||x_priv^T - x^T|| <=
+    Delta_T = sum_{t<=T} ||eps_t||.  eps_t adds to the quantization terms the
+    floating-point roundings of both runs: three ulps of |v| + |x| per run in
+    the z/v updates, and the plaintext matvec's dot-product error
+    gamma_{N_k+1} (|alpha_i| + sum_j |Bbar_ij| |w_j|) with |w_j| <= |w~_j| +
+    Delta_{t-1}.  Then |MSE_priv - MSE_plain| <= (2 ||x_plain - x0|| Delta_T +
+    Delta_T^2) / N."""
     N = len(x0)
-    G, dT = 0.0, 0.0
+    u = 2.0 ** -53
+    dT = 0.0
     zp, vp = np.zeros(N), np.zeros(N)
     for t in range(len(xs)):
-        e = float(np.linalg.norm(round_error_bound(setup, qp, zp, vp, xs[t])))
-        dT = G + e
-        G = 2 * G + e
+        eps = round_error_bound(setup, qp, zp, vp, xs[t])
+        wt = np.abs((gamma2(zp, qp) + gamma2(-np.asarray(vp), qp)) / qp.S + 2 * qp.zmin) + dT
+        for k, (a0, a1) in enumerate(zip(setup.offsets[:-1], setup.offsets[1:])):
+            n = a1 - a0 + 1
+            gam = n * u / (1 - n * u)
+            eps[a0:a1] += gam * (np.abs(setup.alpha[k]) + np.abs(setup.Bbar[k]) @ wt[a0:a1])
+        eps += 6 * np.spacing(np.abs(vp) + np.abs(xs[t]))
+        dT += float(np.linalg.norm(eps))
         zp, vp = zs[t], vs[t]
     return dT, (2 * float(np.linalg.norm(np.asarray(x_plain) - x0)) * dT + dT ** 2) / N

@@ -9,6 +9,8 @@
 //   HI    mad.hi.u32            high half
 //   WIDE  mad.wide.u32          a whole 32x32->64 product plus a 64-bit add
 //   LOHI  mad.lo + mad.hi       a 32x32->64 product from two halves
+// Each step feeds the accumulator back into the multiplier, so no product
+// is loop-invariant (the assembler would otherwise hoist it).
 //   ROW   the carry-chained row of a 64-limb Montgomery product
 //         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc), the exact
 //         instruction pattern of the library's product core; one product per
@@ -53,10 +55,10 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) 
     for (int j = 0; j < 64; ++j) fold ^= t[j];
     fold ^= c0 ^ c1;
   } else if constexpr (KIND == PC2_PROBE_WIDE) {
+    // x <- lo(x) * b + x: the multiplier input changes every step
     uint64_t x[kIlp];
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) x[k] = b + k;
-    const uint32_t a = b | 1u;
     __syncthreads();
     t0 = clock64();
 #pragma unroll 1
@@ -64,19 +66,23 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) 
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[k]) : "r"(a), "r"(b));
+        for (int k = 0; k < kIlp; ++k)
+          asm volatile("{\n .reg .b32 lo, hi;\n mov.b64 {lo, hi}, %0;\n mad.wide.u32 %0, lo, %1, %0;\n}\n"
+                       : "+l"(x[k])
+                       : "r"(b));
       }
     }
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) fold ^= (uint32_t)x[k] ^ (uint32_t)(x[k] >> 32);
   } else {
+    // LO: x <- lo(x b) + c; HI: y <- hi(y b) + c; LOHI: both halves of x b
     uint32_t x[kIlp], y[kIlp];
 #pragma unroll
     for (int k = 0; k < kIlp; ++k) {
       x[k] = b + k;
       y[k] = b ^ k;
     }
-    const uint32_t a = b | 1u;
+    const uint32_t c = b | 1u;
     __syncthreads();
     t0 = clock64();
 #pragma unroll 1
@@ -85,10 +91,14 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) 
       for (int u = 0; u < 16; ++u) {
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) {
-          if constexpr (KIND == PC2_PROBE_LO || KIND == PC2_PROBE_LOHI)
-            asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(x[k]) : "r"(a), "r"(b));
-          if constexpr (KIND == PC2_PROBE_HI || KIND == PC2_PROBE_LOHI)
-            asm volatile("mad.hi.u32 %0, %1, %2, %0;" : "+r"(y[k]) : "r"(a), "r"(b));
+          if constexpr (KIND == PC2_PROBE_LO)
+            asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(b), "r"(c));
+          if constexpr (KIND == PC2_PROBE_HI)
+            asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(y[k]) : "r"(b), "r"(c));
+          if constexpr (KIND == PC2_PROBE_LOHI)
+            asm volatile("{\n .reg .b32 l;\n mad.lo.u32 l, %0, %2, %1;\n mad.hi.u32 %1, %0, %2, %1;\n mov.b32 %0, l;\n}\n"
+                         : "+r"(x[k]), "+r"(y[k])
+                         : "r"(b));
         }
       }
     }

@@ -681,3 +681,18 @@ def probe_mul(device: int, kind: int, blocks_per_sm: int, iters: int, stream=Non
     _check(_probe_mul(device, kind, blocks_per_sm, iters, _stream(stream), ctypes.byref(ops), ctypes.byref(ms),
                       ctypes.byref(cyc), ctypes.byref(sms)), "pc2_probe_mul")
     return {"ops": ops.value, "ms": ms.value, "cycles": cyc.value, "sms": sms.value}
+
+
+# ------------------------------------------------------------------ tensor-core Montgomery experiment
+ENGINE_IMAD, ENGINE_TC = 0, 1
+_mont_sqr = _sig("pc2_mont_sqr", [_vp, _vp, _i, _vp, _sz, _i, _i, _vp, _vp])
+
+
+def mont_sqr(ctx: Context, n: int, x_tiled, count: int, nsq: int, engine: int, out=None, stream=None):
+    """nsq Montgomery squarings mod n (64 words) of a tiled vector (pc2_mont_sqr)."""
+    limbs = max(1, (n.bit_length() + 31) // 32)
+    nw = _words_of(n, limbs)
+    out = empty_tiled(count, limbs, x_tiled.device) if out is None else out
+    _check(_mont_sqr(ctx.h, nw.ctypes.data, limbs, _ptr(x_tiled), count, nsq, engine, _ptr(out), _stream(stream)),
+           "pc2_mont_sqr")
+    return out
