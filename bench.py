@@ -691,6 +691,7 @@ def run_gpu(args):
     global N_PLAIN, GROUPS
     N_PLAIN, GROUPS = args.plaintexts, args.groups
     ctx = pc2.Context(dev)
+    pc2.set_engine(ctx, args.engine)
     key = pc2.Key.generate(NBITS, 2026)
     L2 = 2 * key.limbs
     per_group = N_PLAIN // GROUPS
@@ -755,6 +756,28 @@ def run_gpu(args):
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
     ops = (N_PLAIN + per_group) * world
     value = ops / (ms / 1e3)
+
+    # the same encryption and decryption on each engine of the full-width
+    # powers (integer pipe; tensor cores), outside the step
+    engine_ab = None
+    if rank == 0 and not args.no_engine_ab:
+        engine_ab = {}
+        for name, eng in (("imad", pc2.ENGINE_IMAD), ("tensor_core", pc2.ENGINE_TC)):
+            pc2.set_engine(ctx, eng)
+            r = {}
+            for op, fn in (("encrypt_ms", lambda: pc2.encrypt(ctx, key, dm, SEED, STREAM, e0=e0, out=ct)),
+                           ("decrypt_2p16_ms", lambda: pc2.decrypt(ctx, key, agg, per_group, out=dec))):
+                fn()
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                fn()
+                b.record(st)
+                b.synchronize()
+                r[op] = a.elapsed_time(b)
+            engine_ab[name] = r
+        pc2.set_engine(ctx, args.engine)
+        assert ctx.status() == 0
 
     # decryption of the whole batch (all 2^20 ciphertexts), outside the step
     dec_full_ms = None
@@ -831,7 +854,9 @@ def run_gpu(args):
                    "enc_montmuls_per_elem": mm, "enc_half_width_montmuls_per_elem": mmh,
                    "dec_montmuls_per_elem": dmm, "montmul_limbs": lb, "enc_imads_per_elem": imad_per_elem,
                    "enc_products_per_elem": prod_enc, "dec_products_per_elem": prod_dec,
-                   "hom_sum_products_per_elem": prod_sum, "fractions": fr},
+                   "hom_sum_products_per_elem": prod_sum, "fractions": fr, "engine_ab": engine_ab,
+                   "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 16384,
+                              0: "integer pipe", 1: "tensor cores"}[args.engine]},
         "multiplier_probe": probe,
         "roofline": roof,
         "e2e": {"value": ops / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(m_pinned.numel() * 8),
@@ -884,6 +909,9 @@ def main():
     ap.add_argument("--no-admm-full", action="store_true", help="skip the full-scale 3072-bit ADMM (about 2 min)")
     ap.add_argument("--no-probe", action="store_true", help="skip the multiplier probe (roofline on the nominal peak)")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core Montgomery experiment")
+    ap.add_argument("--engine", type=int, default=-1, choices=[-1, 0, 1],
+                    help="full-width powers at 2048 bits: -1 automatic, 0 integer pipe, 1 tensor cores")
+    ap.add_argument("--no-engine-ab", action="store_true", help="skip the per-engine encryption/decryption timing")
     ap.add_argument("--tc-only", action="store_true", help="run only the tensor-core Montgomery experiment")
     ap.add_argument("--batch-rounds", type=int, default=1)
     ap.add_argument("--plaintexts", type=int, default=N_PLAIN, help="per GPU (reduced sizes are for profiling only)")

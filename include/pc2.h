@@ -89,6 +89,17 @@ int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes);
  * mode 0 automatic (by the estimate of pc2_ctx_set_lanes), 1 never,
  * 2 always.  Results do not change. */
 int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
+/* Engine of the full-width powers of key-owner encryption and CRT
+ * decryption at 2048-bit n (Eq. (itq1), Sec. III-C): PC2_ENGINE_IMAD (the
+ * one-kernel integer-pipe path), PC2_ENGINE_TC (the Montgomery products'
+ * reductions on the tensor cores, see pc2_mont_sqr; three launches per call:
+ * set-up, the powers, finish) or -1 automatic (the tensor cores from
+ * PC2_TC_MIN_COUNT elements on).  Results do not change; other key sizes
+ * always use the integer pipe.  PC2_EINVAL for another value. */
+#define PC2_ENGINE_IMAD 0
+#define PC2_ENGINE_TC 1
+#define PC2_TC_MIN_COUNT 16384
+int pc2_ctx_set_engine(pc2_ctx* ctx, int engine);
 /* Autotuner: times every built lane count x split (on, off) x window
  * width (4..6) of key-owner encryption (ops bit 0) and/or decryption (bit 1)
  * on `count` elements (at most two resident waves of them) and records the
@@ -408,8 +419,6 @@ int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, u
  *  - Asynchronous on `stream`; a wait inside the tensor-core kernel that
  *    runs out raises PC2_ST_TIMEOUT in the context's status word.
  *  - PC2_EINVAL: null pointers, even N, nsq < 0, unknown engine. */
-#define PC2_ENGINE_IMAD 0
-#define PC2_ENGINE_TC 1
 int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const uint32_t* d_x, size_t count, int nsq, int engine,
                  uint32_t* d_y, pc2_stream_t stream);
 

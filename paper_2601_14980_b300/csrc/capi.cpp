@@ -17,6 +17,7 @@
 #include "keys.hpp"
 #include "philox.h"
 #include "pc2_kernels.h"
+#include "pc2_tc.h"
 
 #include "ctx.hpp"
 
@@ -58,7 +59,7 @@ static std::shared_ptr<P> cached(const pc2_key* k, int kind, int window, F make,
   return p;
 }
 
-enum { KIND_ENC_CRT = 1, KIND_ENC_PUB = 2, KIND_DEC = 3, KIND_HOM = 64 };  // KIND_HOM + operands (1..32)
+enum { KIND_ENC_CRT = 1, KIND_ENC_PUB = 2, KIND_DEC = 3, KIND_TC = 4, KIND_HOM = 64 };  // KIND_HOM + operands (1..32)
 
 static uint32_t* ctx_scratch(void* c, size_t bytes) {
   pc2_ctx* ctx = static_cast<pc2_ctx*>(c);
@@ -200,6 +201,21 @@ static int with_n2_lanes(pc2_ctx* ctx, size_t count, Fn fn) {
   return PC2_EUNSUPPORTED;
 }
 
+// The tensor-core blocks of p^2 and q^2 (2048-bit keys), cached per key.
+static std::shared_ptr<TcKeyMods> tc_mods(const pc2_key* key, int* rc) {
+  return cached<TcKeyMods>(key, KIND_TC, 0, [&](TcKeyMods& K) {
+    uint32_t w[tc::kL];
+    mul(key->p, key->p).to_words(w, tc::kL);
+    if (!tc::build_mod(w, K.p2)) return PC2_EKEY;
+    mul(key->q, key->q).to_words(w, tc::kL);
+    if (!tc::build_mod(w, K.q2)) return PC2_EKEY;
+    return PC2_OK;
+  }, rc);
+}
+static bool use_tc(const pc2_ctx* ctx, size_t count) {
+  return ctx->engine == PC2_ENGINE_TC || (ctx->engine < 0 && count >= (size_t)PC2_TC_MIN_COUNT);
+}
+
 template <int Lh>
 static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const uint32_t* mw, size_t count,
                    uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* out, cudaStream_t st) {
@@ -215,6 +231,13 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
   P->stream = stream;
   P->e0 = e0;
   P->mwords = mw ? Lh : 2;
+  if constexpr (Lh == 64) {
+    if (use_tc(ctx, count)) {
+      auto K = tc_mods(key, &rc);
+      if (!K) return rc;
+      return launch_enc_crt_tc(*P, *K, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
+    }
+  }
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
     if (cfg.split) return launch_enc_crt2<Lh, T>(*P, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
@@ -302,6 +325,13 @@ static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
   int rc;
   auto P = cached<DecParams<Lh>>(key, KIND_DEC, w, [&](DecParams<Lh>& p) { return make_dec<Lh>(*key, w, p); }, &rc);
   if (!P) return rc;
+  if constexpr (Lh == 64) {
+    if (use_tc(ctx, count)) {
+      auto K = tc_mods(key, &rc);
+      if (!K) return rc;
+      return launch_dec_crt_tc(*P, *K, ct, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
+    }
+  }
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
     if (cfg.split) return launch_dec_crt2<Lh, T>(*P, ct, count, out, ctx_scratch, ctx, ctx->sms, st, base);
@@ -504,6 +534,12 @@ int pc2_ctx_set_lanes(pc2_ctx* ctx, int lanes) {
 int pc2_ctx_set_split(pc2_ctx* ctx, int mode) {
   if (!ctx || mode < 0 || mode > 2) return PC2_EINVAL;
   ctx->split = mode;
+  return PC2_OK;
+}
+
+int pc2_ctx_set_engine(pc2_ctx* ctx, int engine) {
+  if (!ctx || (engine != -1 && engine != PC2_ENGINE_IMAD && engine != PC2_ENGINE_TC)) return PC2_EINVAL;
+  ctx->engine = engine;
   return PC2_OK;
 }
 

@@ -21,6 +21,7 @@ struct pc2_ctx {
   int window = 0;         // 0 = automatic
   int lanes = 0;          // 0 = automatic (tuned table, else fill heuristic)
   int split = 0;          // CRT halves in parallel: 0 automatic, 1 never, 2 whenever lanes > 1
+  int engine = -1;        // full-width powers at 2048-bit n: -1 automatic, 0 integer pipe, 1 tensor cores
   // autotuned (lanes, window, split) per (op, limbs, ceil(log2 of the element count))
   std::mutex tune_mu;
   std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;

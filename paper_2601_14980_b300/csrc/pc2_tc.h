@@ -1,0 +1,49 @@
+// pc2_tc.h -- host-side declarations of the tensor-core Montgomery path
+// (tc_core.cuh, tc_paillier.cu): the per-modulus constant block and the
+// launchers of encryption and decryption at 2048-bit n.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pc2_kernels.h"
+#include "pc2_params.h"
+
+namespace pc2 {
+namespace tc {
+
+constexpr int kL = 64;        // limbs of the modulus (2048 bits)
+constexpr int kB1Rows = 256;  // Toeplitz(N') slice rows: output columns 0..255
+constexpr int kB2Rows = 272;  // Toeplitz(N) slice rows: output columns 16 s .. 16 s + 271
+
+// A modulus N (64 words) with its two Toeplitz slices (bf16 bits, K-major,
+// no swizzle: K-block kb of 8 columns is a [rows x 8] row-major slab).
+struct alignas(16) Mod {
+  uint32_t n[kL];
+  uint16_t b1[kB1Rows * 16];  // digits of N' = -N^-1 mod 2^2048
+  uint16_t b2[kB2Rows * 16];  // digits of N
+  uint32_t np0;               // -N^-1 mod 2^32
+  uint32_t pad_[3];
+};
+
+// Builds the block of an odd N (host).  False for an even N.
+bool build_mod(const uint32_t* n64, Mod& M);
+
+}  // namespace tc
+
+// The blocks of p^2 and q^2 of a 2048-bit key.
+struct TcKeyMods {
+  tc::Mod p2, q2;
+};
+
+// Key-owner encryption / CRT decryption at 2048-bit n with the full-width
+// powers on the tensor cores; same arguments and results as launch_enc_crt /
+// launch_dec_crt.
+int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint64_t* m64, const uint32_t* mwide,
+                      size_t count, uint32_t* out, ScratchFn scratch_fn, void* sctx, int* status, int sms,
+                      cudaStream_t st, size_t base);
+int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t* ct, size_t count, uint32_t* out,
+                      ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base);
+
+}  // namespace pc2

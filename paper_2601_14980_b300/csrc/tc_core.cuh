@@ -1,0 +1,362 @@
+// tc_core.cuh -- Montgomery products of 2048-bit operands with the
+// reduction on the tensor cores (tcgen05.mma, bf16 digits, exact FP32
+// column sums), for the modular exponentiations of libpc2.
+//
+// The part of a modular product that is a dense contraction with an operand
+// shared by all elements is the reduction (the paper's Alg. 2 recasts
+// big-integer products as low-bitwidth vector/matrix operations): in
+// separated operand scanning,
+//   T = a b,  m = (T mod R) N' mod R,  U = (T + m N) / R   (N' = -N^-1 mod R),
+// and both m and m N multiply a per-element vector by the modulus' fixed N'
+// or N.  Over 8-bit digits (x = sum_k x_k 256^k) the column sums
+// C_j = sum_k x_k y_{j-k} are an [elements x digits] matrix times a
+// Toeplitz matrix of the fixed operand's digits.  Digits 0..255 are exact in
+// bf16 and every column sum stays below 256 * 255^2 < 2^24, so the FP32
+// accumulation of kind::f16 tcgen05.mma is exact.
+//
+// A CTA owns tiles of 128 elements (MMA M = 128, TMEM lane e = element e):
+// warps 0-3 hold one element per thread, warp 4 allocates 256 TMEM columns
+// and serves the MMAs.  One product a <- a b / R mod N:
+//   1. warps 0-3: T = a b by rows on the integer pipe (a in registers, b's
+//      word i read from shared memory before row i); each finished low word
+//      of T is written as four bf16 digits into the A tile;
+//   2. warp 4: m-columns = A x Toeplitz(N'), columns 0..255, into TMEM;
+//   3. warps 0-3: carries over the columns give m, whose digits go into the
+//      A tile;
+//   4. warp 4: columns 256..511 of m N; after they are read, columns
+//      240..255, which fix the carry out of the low half;
+//   5. warps 0-3: U = T_hi + Hi + carry, then U - N when U >= N.
+// For every K-slice s of 16 digits the Toeplitz operand is the same
+// [rows x 16] matrix once the slice's output columns start 16 s further, so
+// a fixed operand costs one small slice (8 KB for N', 8.5 KB for N), and the
+// A tile (64 KB) also holds each element's operand b: word i sits in the
+// first four bytes of the 8-byte slot that T word i overwrites after row i.
+// Shared memory per CTA: 81 KB; two CTAs per SM (2 x 256 TMEM columns).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mont.cuh"
+#include "pc2_tc.h"
+
+namespace pc2 {
+namespace tc {
+
+constexpr int kD = 4 * kL;           // 8-bit digits per operand
+constexpr int kTileE = 128;          // elements per tile (MMA M)
+constexpr int kThreads = 160;        // warps 0-3 compute, warp 4 serves the MMAs
+constexpr int kSlab = kTileE * 16;   // bytes of one 8-digit K-block of the A tile
+constexpr int kAbytes = (kD / 8) * kSlab;   // 64 KB
+constexpr int kB1bytes = kB1Rows * 32;      // 8 KB
+constexpr int kB2bytes = kB2Rows * 32;      // 8.5 KB
+constexpr int kSmem = kAbytes + kB1bytes + kB2bytes + 64;
+constexpr uint32_t kTmemCols = 256;
+constexpr long kSpin = 1L << 20;     // bounded waits (a tile's MMAs take microseconds)
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Waits for phase `parity` of the barrier; false after kSpin trips.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (long it = 0; it < kSpin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// SMEM matrix descriptor, no swizzle, K-major: LBO = bytes between K-adjacent
+// 8x16-byte core matrices, SBO = bytes between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileE >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Named barrier 1: the compute warps arrive, the serving warp waits.
+__device__ __forceinline__ void bar_arrive1() { asm volatile("bar.arrive 1, %0;" ::"n"(kThreads) : "memory"); }
+__device__ __forceinline__ void bar_sync1() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+// 16 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// An exact column sum (an integer below 2^24 held in f32) as an integer.
+__device__ __forceinline__ uint64_t col(uint32_t bits) { return (uint64_t)__float2uint_rz(__uint_as_float(bits)); }
+// The four digits of word w as bf16 (exact: 0..255), two per 32-bit word.
+__device__ __forceinline__ uint2 word_digits(uint32_t w) {
+  const uint32_t f0 = __float_as_uint(__uint2float_rn(w & 0xffu));
+  const uint32_t f1 = __float_as_uint(__uint2float_rn((w >> 8) & 0xffu));
+  const uint32_t f2 = __float_as_uint(__uint2float_rn((w >> 16) & 0xffu));
+  const uint32_t f3 = __float_as_uint(__uint2float_rn(w >> 24));
+  return make_uint2(__byte_perm(f0, f1, 0x7632), __byte_perm(f2, f3, 0x7632));
+}
+// Byte offset of word i of element e in the A tile (digits 4i..4i+3 of row e).
+__device__ __forceinline__ uint32_t slot_off(int i, int e) { return (uint32_t)((i >> 1) * kSlab + e * 16 + (i & 1) * 8); }
+
+// Shared-memory layout and TMEM of one CTA.
+struct Smem {
+  uint8_t* A;
+  uint8_t* B1;
+  uint8_t* B2;
+  uint64_t* bar;
+  volatile uint32_t* cmd;   // 1: another product follows, 0: stop
+  uint32_t* tmem_slot;
+};
+__device__ __forceinline__ Smem smem_layout(uint8_t* base) {
+  Smem s;
+  s.A = base;
+  s.B1 = base + kAbytes;
+  s.B2 = s.B1 + kB1bytes;
+  s.bar = reinterpret_cast<uint64_t*>(s.B2 + kB2bytes);
+  s.cmd = reinterpret_cast<volatile uint32_t*>(s.bar + 1);
+  s.tmem_slot = const_cast<uint32_t*>(s.cmd) + 1;
+  return s;
+}
+
+// Start of the kernel (all threads): the Toeplitz slices into shared memory,
+// the barrier, 256 TMEM columns.  Returns the TMEM base address.
+__device__ __forceinline__ uint32_t setup(const Smem& s, const Mod& M) {
+  const uint4* s1 = reinterpret_cast<const uint4*>(M.b1);
+  const uint4* s2 = reinterpret_cast<const uint4*>(M.b2);
+  for (int i = threadIdx.x; i < kB1bytes / 16; i += kThreads) reinterpret_cast<uint4*>(s.B1)[i] = s1[i];
+  for (int i = threadIdx.x; i < kB2bytes / 16; i += kThreads) reinterpret_cast<uint4*>(s.B2)[i] = s2[i];
+  if (threadIdx.x == 0) {
+    mbar_init(s.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s.tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  async_proxy_fence();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  return *s.tmem_slot;
+}
+
+// End of the kernel (all threads): release the TMEM columns.
+__device__ __forceinline__ void teardown(uint32_t tmem) {
+  fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 4) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Warp 4: issues the three MMA groups of every product until told to stop.
+__device__ __forceinline__ void serve(const Smem& s, uint32_t tmem) {
+  const bool leader = (threadIdx.x & 31) == 0;
+  const uint32_t a_base = smem_addr(s.A), b1_base = smem_addr(s.B1), b2_base = smem_addr(s.B2);
+  for (;;) {
+    bar_sync1();
+    if (*s.cmd == 0u) break;
+    fence_after();
+    // m-columns: slice s adds A[:, 16s..16s+15] x B1[0..255-16s] into columns 16s..255
+    if (leader) {
+      for (int k = 0; k < kD / 16; ++k)
+        mma_bf16(tmem + 16 * k, sdesc(a_base + 2 * k * kSlab, kSlab, 128), sdesc(b1_base, kB1Rows * 16, 128),
+                 idesc_bf16(256 - 16 * k), k > 0);
+      mma_commit(s.bar);
+    }
+    __syncwarp();
+    // columns 256..511 of m N into TMEM columns 0..255 (slice 15 first: it covers them all)
+    bar_sync1();
+    fence_after();
+    if (leader) {
+      for (int k = kD / 16 - 1; k >= 0; --k)
+        mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
+                 sdesc(b2_base + (256 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16 * k + 16), k != kD / 16 - 1);
+      mma_commit(s.bar);
+    }
+    __syncwarp();
+    // columns 240..255 of m N into TMEM columns 0..15
+    bar_sync1();
+    fence_after();
+    if (leader) {
+      for (int k = kD / 16 - 1; k >= 0; --k)
+        mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
+                 sdesc(b2_base + (240 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16), k != kD / 16 - 1);
+      mma_commit(s.bar);
+    }
+    __syncwarp();
+  }
+}
+
+// Compute warps: tells warp 4 that no product follows (all compute threads call it once).
+__device__ __forceinline__ void stop(const Smem& s) {
+  if (threadIdx.x == 0) *s.cmd = 0u;
+  bar_arrive1();
+}
+
+// Per-thread state of the compute side.
+struct State {
+  uint32_t phase;
+  bool ok;
+};
+
+// Compute warps, element e = threadIdx.x: a <- a b / R mod N, where b's words
+// are already in their slots of the A tile (write_b_*).
+__device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
+                                        State& st) {
+  const int e = threadIdx.x;
+  const int warp = e >> 5;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  uint8_t* A = s.A;
+  // 1. T = a b; finished low words become digits
+  uint32_t t[kL];
+#pragma unroll
+  for (int j = 0; j < kL; ++j) t[j] = 0u;
+  uint32_t c0 = 0u, c1 = 0u, nz = 0u, top0 = 0u, top1 = 0u;
+#pragma unroll 1
+  for (int i = 0; i < kL; ++i) {
+    const uint32_t bi = *reinterpret_cast<const uint32_t*>(A + slot_off(i, e));
+    row_mac<kL>(t, c0, c1, RegA<kL>{a}, bi);
+    const uint32_t w = t[0];
+    nz |= w;
+    top0 = i == kL - 2 ? w : top0;
+    top1 = i == kL - 1 ? w : top1;
+    *reinterpret_cast<uint2*>(A + slot_off(i, e)) = word_digits(w);
+#pragma unroll
+    for (int j = 0; j < kL - 1; ++j) t[j] = t[j + 1];
+    t[kL - 1] = c0;
+    c0 = c1;
+    c1 = 0u;
+  }
+  // t = T_hi (T < N^2 < 2^4096)
+  if (e == 0) *s.cmd = 1u;
+  async_proxy_fence();
+  fence_before();
+  bar_arrive1();
+  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
+  st.phase ^= 1u;
+  fence_after();
+  // 3. m = (sum_j C_j 256^j) mod R from columns 0..255; its digits into the A tile
+  {
+    uint64_t carry = 0;
+#pragma unroll 1
+    for (int ch = 0; ch < 16; ++ch) {
+      uint32_t r[16];
+      tmem_ld16(lane_base + 16 * ch, r);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const uint64_t v = carry + col(r[4 * w]) + (col(r[4 * w + 1]) << 8) + (col(r[4 * w + 2]) << 16) +
+                           (col(r[4 * w + 3]) << 24);
+        carry = v >> 32;
+        *reinterpret_cast<uint2*>(A + slot_off(4 * ch + w, e)) = word_digits((uint32_t)v);
+      }
+    }
+  }
+  async_proxy_fence();
+  fence_before();
+  bar_arrive1();
+  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
+  st.phase ^= 1u;
+  fence_after();
+  // 5a. t += Hi = sum_j C_{256+j} 256^j
+  uint32_t over = 0u;  // bit 2048 of the running sum
+  {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int ch = 0; ch < 16; ++ch) {
+      uint32_t r[16];
+      tmem_ld16(lane_base + 16 * ch, r);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const uint64_t v = carry + t[4 * ch + w] + col(r[4 * w]) + (col(r[4 * w + 1]) << 8) +
+                           (col(r[4 * w + 2]) << 16) + (col(r[4 * w + 3]) << 24);
+        t[4 * ch + w] = (uint32_t)v;
+        carry = v >> 32;
+      }
+    }
+    over = (uint32_t)carry;
+  }
+  fence_before();
+  bar_arrive1();
+  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
+  st.phase ^= 1u;
+  fence_after();
+  // 5b. carry out of the low half: T_lo + Lo = c R, Lo = sum_{j<256} C_j 256^j.
+  // Lo = F + c' R with F = (R - T_lo) mod R; c' = round((Lo - F) / R) from
+  // columns 248..255 and the top 64 bits of F (error below 2^-39).
+  {
+    uint32_t r[16];
+    tmem_ld16(lane_base, r);
+    unsigned __int128 X = 0;
+#pragma unroll
+    for (int l = 15; l >= 8; --l) X = (X << 8) + (unsigned __int128)col(r[l]);
+    const uint64_t ttop = ((uint64_t)top1 << 32) | top0;
+    const unsigned __int128 Ftop = nz ? ((unsigned __int128)1 << 64) - ttop : 0;
+    const __int128 d = (__int128)X - (__int128)Ftop + ((__int128)1 << 63);
+    const uint64_t c = (uint64_t)(d >> 64) + (nz ? 1u : 0u);
+    uint64_t v = (uint64_t)t[0] + (uint32_t)c;
+    t[0] = (uint32_t)v;
+    v = (v >> 32) + t[1] + (uint32_t)(c >> 32);
+    t[1] = (uint32_t)v;
+    v >>= 32;
+#pragma unroll
+    for (int j = 2; j < kL; ++j) {
+      v += t[j];
+      t[j] = (uint32_t)v;
+      v >>= 32;
+    }
+    over += (uint32_t)v;
+  }
+  // U < 2N: subtract N when U >= N
+  uint32_t br;
+  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(a[0]) : "r"(t[0]), "r"(n[0]));
+#pragma unroll
+  for (int j = 1; j < kL; ++j) asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(a[j]) : "r"(t[j]), "r"(n[j]));
+  asm volatile("subc.u32 %0, 0, 0;" : "=r"(br));
+  const bool keep = over == 0u && br != 0u;
+#pragma unroll
+  for (int j = 0; j < kL; ++j) a[j] = keep ? t[j] : a[j];
+}
+
+// b = the thread's own a (a squaring).
+__device__ __forceinline__ void write_b_self(const Smem& s, const uint32_t (&a)[kL]) {
+#pragma unroll
+  for (int j = 0; j < kL; ++j) *reinterpret_cast<uint32_t*>(s.A + slot_off(j, threadIdx.x)) = a[j];
+}
+// b = word j at src[j * stride] (a table entry in global memory).
+__device__ __forceinline__ void write_b_global(const Smem& s, const uint32_t* src, size_t stride) {
+#pragma unroll 8
+  for (int j = 0; j < kL; ++j)
+    *reinterpret_cast<uint32_t*>(s.A + slot_off(j, threadIdx.x)) = src[(size_t)j * stride];
+}
+
+}  // namespace tc
+}  // namespace pc2

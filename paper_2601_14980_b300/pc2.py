@@ -472,6 +472,14 @@ def autotune(ctx: Context, key: Key, count: int, encrypt: bool = True, decrypt: 
 _ctx_set_split = _sig("pc2_ctx_set_split", [_vp, _i])
 
 
+_set_engine = _sig("pc2_ctx_set_engine", [_vp, _i])
+
+
+def set_engine(ctx: Context, engine: int):
+    """Full-width powers at 2048-bit n: -1 automatic, ENGINE_IMAD, ENGINE_TC (pc2_ctx_set_engine)."""
+    _check(_set_engine(ctx.h, engine), "pc2_ctx_set_engine")
+
+
 def set_split(ctx: Context, mode: int):
     """CRT halves in parallel: 0 automatic, 1 never, 2 always."""
     _check(_ctx_set_split(ctx.h, mode), "pc2_ctx_set_split")
