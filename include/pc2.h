@@ -402,6 +402,41 @@ int pc2_server_wait(pc2_server* server, uint64_t ticket, double timeout_s, doubl
 /* Requests completed, steps launched, work items run, peak arena bytes in use. */
 int pc2_server_stats(pc2_server* server, uint64_t* completed, uint64_t* steps, uint64_t* items, size_t* arena_peak);
 
+/* ---- collaborative CRT split between the master and an edge node ---- *
+ * Sec. IV-C, Algorithm 3: edge node k holds p^2 and phi(p^2) (sent once by
+ * the master) and computes the p^2 half of the master's encryptions and the
+ * residues mod p^2 of its own ciphertexts; the master computes the q^2
+ * halves and recombines (Lemmas 1-2, Eq. (gA-C-B)).  The obfuscation O(.),
+ * which the paper leaves undefined, is an additive mask: O(w) = w + kappa.
+ * Exchange 1: the master sends O(w) (pc2_collab_mask) and the edge
+ * returns c'_masked = g^(O(w) mod phi(p^2)) r^n mod p^2
+ * (pc2_collab_edge_encrypt); the master removes the mask with
+ * g^(phi(p^2) - kappa mod phi(p^2)) and forms E(w; r) (pc2_collab_master_
+ * encrypt): the same ciphertext as pc2_encrypt with the same seed, stream
+ * and counters.  For decryption the edge sends x-hat mod p^2
+ * (pc2_collab_edge_reduce) and the master decrypts from it and its own
+ * residue mod q^2 (pc2_collab_master_decrypt), as pc2_decrypt.
+ *  - Keys of 256 to 2048 bits (PC2_EUNSUPPORTED otherwise); `key` must be
+ *    private (PC2_EKEY).  The edge calls read only p^2, phi(p^2), n and the
+ *    schedule of the power r^n mod p^2 from it.
+ *  - Device vectors in the tiled layout: w uint64 plaintexts (quantized
+ *    values, below 2^64); kappa, O(w) and the p^2 halves/residues L words
+ *    (L = words of n); ciphertexts 2L words; plaintexts L words.
+ *  - kappa must be below 2^(32 L) - 2^64 so that O(w) fits L words; a carry
+ *    out raises PC2_ST_RANGE in the status word.
+ *  - Asynchronous on `stream`; scratch from the context. */
+int pc2_collab_mask(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_w, const uint32_t* d_kappa, size_t count,
+                    uint32_t* d_ow, pc2_stream_t stream);
+int pc2_collab_edge_encrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ow, size_t count, uint64_t seed,
+                            uint32_t stream, uint64_t e0, uint32_t* d_cp, pc2_stream_t cstream);
+int pc2_collab_master_encrypt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* d_w, const uint32_t* d_kappa,
+                              const uint32_t* d_cp, size_t count, uint64_t seed, uint32_t stream, uint64_t e0,
+                              uint32_t* d_ct, pc2_stream_t cstream);
+int pc2_collab_edge_reduce(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t count, uint32_t* d_cp,
+                           pc2_stream_t cstream);
+int pc2_collab_master_decrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, const uint32_t* d_cp,
+                              size_t count, uint32_t* d_m, pc2_stream_t cstream);
+
 /* ---- Montgomery squarings on the tensor cores (an experiment) ------- *
  * nsq Montgomery squarings of each element: y = x^(2^nsq) R^-(2^nsq - 1)
  * mod N, R = 2^(32 limbs), the dominant operation of the fixed-exponent

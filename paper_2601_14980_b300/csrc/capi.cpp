@@ -350,6 +350,16 @@ template std::shared_ptr<DecParams<64>> dec_params<64>(const pc2_key*, int*);
 template std::shared_ptr<DecParams<96>> dec_params<96>(const pc2_key*, int*);
 template std::shared_ptr<DecParams<128>> dec_params<128>(const pc2_key*, int*);
 
+template <int Lh>
+std::shared_ptr<EncCrtParams<Lh>> enc_params(const pc2_key* key, int* rc) {
+  return cached<EncCrtParams<Lh>>(key, KIND_ENC_CRT, 0,
+                                  [&](EncCrtParams<Lh>& p) { return make_enc_crt<Lh>(*key, 0, p); }, rc);
+}
+template std::shared_ptr<EncCrtParams<8>> enc_params<8>(const pc2_key*, int*);
+template std::shared_ptr<EncCrtParams<16>> enc_params<16>(const pc2_key*, int*);
+template std::shared_ptr<EncCrtParams<32>> enc_params<32>(const pc2_key*, int*);
+template std::shared_ptr<EncCrtParams<64>> enc_params<64>(const pc2_key*, int*);
+
 template <int L2>
 static int hom_sum(pc2_ctx* ctx, const pc2_key* key, const uint32_t* const* srcs, size_t groups, size_t count,
                    uint32_t* out, cudaStream_t st, size_t base = 0) {

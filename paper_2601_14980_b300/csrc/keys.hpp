@@ -39,5 +39,7 @@ template <int L2> int make_hom(const pc2_key& k, int w, int ngroups, HomParams<L
 // The decryption parameter block of a key from the per-key host cache
 // (built on first use; automatic window).
 template <int Lh> std::shared_ptr<DecParams<Lh>> dec_params(const pc2_key* k, int* rc);
+// The key-owner encryption block, likewise (automatic window).
+template <int Lh> std::shared_ptr<EncCrtParams<Lh>> enc_params(const pc2_key* k, int* rc);
 
 }  // namespace pc2

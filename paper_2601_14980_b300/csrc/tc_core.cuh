@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "mont.cuh"
 #include "pc2_tc.h"
@@ -228,27 +229,30 @@ struct State {
   bool ok;
 };
 
-// Compute warps, element e = threadIdx.x: a <- a b / R mod N, where b's words
-// are already in their slots of the A tile (write_b_*).
-__device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
-                                        State& st) {
+// Result of the product phase: t = T_hi (words 64..127 of T), the low words
+// already in the A tile as digits; nz = (T_lo != 0); top = words 62, 63 of T.
+struct Prod {
+  uint32_t nz, top0, top1;
+};
+
+// Product phase of a general product, element e = threadIdx.x: T = a b with
+// b's words in their slots of the A tile (write_b_*), by rows on the integer
+// pipe; each finished low word of T becomes four digits in its slot.
+__device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
   const int e = threadIdx.x;
-  const int warp = e >> 5;
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
   uint8_t* A = s.A;
-  // 1. T = a b; finished low words become digits
-  uint32_t t[kL];
 #pragma unroll
   for (int j = 0; j < kL; ++j) t[j] = 0u;
-  uint32_t c0 = 0u, c1 = 0u, nz = 0u, top0 = 0u, top1 = 0u;
+  uint32_t c0 = 0u, c1 = 0u;
+  Prod pr{0u, 0u, 0u};
 #pragma unroll 1
   for (int i = 0; i < kL; ++i) {
     const uint32_t bi = *reinterpret_cast<const uint32_t*>(A + slot_off(i, e));
     row_mac<kL>(t, c0, c1, RegA<kL>{a}, bi);
     const uint32_t w = t[0];
-    nz |= w;
-    top0 = i == kL - 2 ? w : top0;
-    top1 = i == kL - 1 ? w : top1;
+    pr.nz |= w;
+    pr.top0 = i == kL - 2 ? w : pr.top0;
+    pr.top1 = i == kL - 1 ? w : pr.top1;
     *reinterpret_cast<uint2*>(A + slot_off(i, e)) = word_digits(w);
 #pragma unroll
     for (int j = 0; j < kL - 1; ++j) t[j] = t[j + 1];
@@ -256,7 +260,87 @@ __device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32
     c0 = c1;
     c1 = 0u;
   }
-  // t = T_hi (T < N^2 < 2^4096)
+  return pr;  // T < N^2 < 2^4096: nothing is left above t
+}
+
+// Row i of the squaring's cross products: C += a_i (a_{i+1} .. a_63) at
+// positions 2i+1 .. i+64 (carry into i+65); positions up to 2i+2 are then
+// final, and those below 64 are parked in their slots of the A tile.
+template <int I>
+__device__ __forceinline__ void sqr_row(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
+  mad_lo_cc(C[2 * I + 1], a[I], a[I + 1]);
+#pragma unroll
+  for (int j = I + 2; j < kL; ++j) madc_lo_cc(C[I + j], a[I], a[j]);
+  addc_z(C[I + kL]);
+  mad_hi_cc(C[2 * I + 2], a[I], a[I + 1]);
+#pragma unroll
+  for (int j = I + 2; j < kL; ++j) madc_hi_cc(C[I + j + 1], a[I], a[j]);
+  C[I + kL + 1] = 0u;
+  addc_z(C[I + kL + 1]);
+  if constexpr (2 * I + 1 < kL) *reinterpret_cast<uint32_t*>(A + slot_off(2 * I + 1, e)) = C[2 * I + 1];
+  if constexpr (2 * I + 2 < kL) *reinterpret_cast<uint32_t*>(A + slot_off(2 * I + 2, e)) = C[2 * I + 2];
+}
+template <int I, int END>
+__device__ __forceinline__ void sqr_rows(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
+  if constexpr (I < END) {
+    sqr_row<I>(C, a, A, e);
+    sqr_rows<I + 1, END>(C, a, A, e);
+  }
+}
+
+// Product phase of a squaring, element e = threadIdx.x: T = a^2 = 2 C + D
+// with C = sum_{i<j} a_i a_j 2^(32(i+j)) (rows of shrinking length, fully
+// unrolled, a in registers) and D = sum_i a_i^2 2^(64 i): 2080 word products
+// instead of 4096.  Finished words of C below 64 wait in their slots of the
+// A tile; one pass then doubles C, adds D and writes the low words' digits.
+__device__ __forceinline__ Prod product_sqr(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
+  const int e = threadIdx.x;
+  uint8_t* A = s.A;
+  uint32_t C[2 * kL];
+#pragma unroll
+  for (int k = 0; k < kL + 2; ++k) C[k] = 0u;
+  Prod pr{0u, 0u, 0u};
+  uint32_t prev = 0u;
+  uint64_t carry = 0;
+  // T_k = 2 C_k + D_k + carry, for k in [K0, K1)
+  auto pass = [&](auto k0, auto k1) {
+#pragma unroll
+    for (int k = decltype(k0)::value; k < decltype(k1)::value; ++k) {
+      const uint32_t ck = k == 0 ? 0u : (k < kL ? *reinterpret_cast<const uint32_t*>(A + slot_off(k, e)) : C[k]);
+      const uint32_t dbl = (ck << 1) | (prev >> 31);
+      prev = ck;
+      const uint32_t ai = a[k >> 1];
+      const uint32_t dk = (k & 1) ? __umulhi(ai, ai) : ai * ai;
+      const uint64_t v = carry + dbl + dk;
+      const uint32_t w = (uint32_t)v;
+      carry = v >> 32;
+      if (k < kL) {
+        pr.nz |= w;
+        if (k == kL - 2) pr.top0 = w;
+        if (k == kL - 1) pr.top1 = w;
+        *reinterpret_cast<uint2*>(A + slot_off(k, e)) = word_digits(w);
+      } else {
+        t[k - kL] = w;
+      }
+    }
+  };
+  // rows 0..31 finish every position below 65; the low half's pass then
+  // frees a_0 .. a_31 before the remaining rows
+  sqr_rows<0, kL / 2>(C, a, A, e);
+  pass(std::integral_constant<int, 0>(), std::integral_constant<int, kL>());
+  sqr_rows<kL / 2, kL - 1>(C, a, A, e);
+  pass(std::integral_constant<int, kL>(), std::integral_constant<int, 2 * kL>());
+  return pr;
+}
+
+// Reduction phase, element e = threadIdx.x: from T (t = T_hi, the low words'
+// digits in the A tile) to a = T / R mod N with the tensor cores.
+__device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], const Prod& pr, const Smem& s,
+                                       uint32_t tmem, const uint32_t* n, State& st) {
+  const int e = threadIdx.x;
+  const int warp = e >> 5;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  uint8_t* A = s.A;
   if (e == 0) *s.cmd = 1u;
   async_proxy_fence();
   fence_before();
@@ -318,10 +402,10 @@ __device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32
     unsigned __int128 X = 0;
 #pragma unroll
     for (int l = 15; l >= 8; --l) X = (X << 8) + (unsigned __int128)col(r[l]);
-    const uint64_t ttop = ((uint64_t)top1 << 32) | top0;
-    const unsigned __int128 Ftop = nz ? ((unsigned __int128)1 << 64) - ttop : 0;
+    const uint64_t ttop = ((uint64_t)pr.top1 << 32) | pr.top0;
+    const unsigned __int128 Ftop = pr.nz ? ((unsigned __int128)1 << 64) - ttop : 0;
     const __int128 d = (__int128)X - (__int128)Ftop + ((__int128)1 << 63);
-    const uint64_t c = (uint64_t)(d >> 64) + (nz ? 1u : 0u);
+    const uint64_t c = (uint64_t)(d >> 64) + (pr.nz ? 1u : 0u);
     uint64_t v = (uint64_t)t[0] + (uint32_t)c;
     t[0] = (uint32_t)v;
     v = (v >> 32) + t[1] + (uint32_t)(c >> 32);
@@ -344,6 +428,22 @@ __device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32
   const bool keep = over == 0u && br != 0u;
 #pragma unroll
   for (int j = 0; j < kL; ++j) a[j] = keep ? t[j] : a[j];
+}
+
+
+// a <- a b / R mod N, b's words already in their slots (write_b_*).
+__device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
+                                        State& st) {
+  uint32_t t[kL];
+  const Prod pr = product_rows(a, t, s);
+  reduce(a, t, pr, s, tmem, n, st);
+}
+// a <- a^2 / R mod N (no operand slots needed).
+__device__ __forceinline__ void montsqr(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
+                                        State& st) {
+  uint32_t t[kL];
+  const Prod pr = product_sqr(a, t, s);
+  reduce(a, t, pr, s, tmem, n, st);
 }
 
 // b = the thread's own a (a squaring).

@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
 #pragma unroll
       for (int j = 0; j < kL; ++j) a[j] = x[pc2::tiled_index(g, j, kL)];
       for (int it = 0; it < nsq; ++it) {
-        tc::write_b_self(s, a);
-        tc::montmul(a, s, tmem, P.m.n, st);
+        tc::montsqr(a, s, tmem, P.m.n, st);
       }
       if (valid) {
 #pragma unroll

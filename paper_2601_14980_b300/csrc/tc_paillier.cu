@@ -97,9 +97,12 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
           }
           if (!more) break;
         }
-        if (src < 0) tc::write_b_self(s, a);
-        else tc::write_b_global(s, entry(src), ts);
-        tc::montmul(a, s, tmem, P.m.n, st);
+        if (src < 0) {
+          tc::montsqr(a, s, tmem, P.m.n, st);
+        } else {
+          tc::write_b_global(s, entry(src), ts);
+          tc::montmul(a, s, tmem, P.m.n, st);
+        }
         if (phase == 0) {  // x^2: keep it, restart from x
           uint32_t* t2 = entry(ntab);
           const uint32_t* t0 = entry(0);

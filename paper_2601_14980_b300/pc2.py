@@ -704,3 +704,46 @@ def mont_sqr(ctx: Context, n: int, x_tiled, count: int, nsq: int, engine: int, o
     _check(_mont_sqr(ctx.h, nw.ctypes.data, limbs, _ptr(x_tiled), count, nsq, engine, _ptr(out), _stream(stream)),
            "pc2_mont_sqr")
     return out
+
+
+# ------------------------------------------------------------------ collaborative CRT split (Algorithm 3)
+_collab_mask = _sig("pc2_collab_mask", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
+_collab_edge_encrypt = _sig("pc2_collab_edge_encrypt", [_vp, _vp, _vp, _sz, _u64, _u32, _u64, _vp, _vp])
+_collab_master_encrypt = _sig("pc2_collab_master_encrypt", [_vp, _vp, _vp, _vp, _vp, _sz, _u64, _u32, _u64, _vp, _vp])
+_collab_edge_reduce = _sig("pc2_collab_edge_reduce", [_vp, _vp, _vp, _sz, _vp, _vp])
+_collab_master_decrypt = _sig("pc2_collab_master_decrypt", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
+
+
+def collab_mask(ctx: Context, key: Key, w, kappa, count: int, out=None, stream=None):
+    out = empty_tiled(count, key.limbs, w.device) if out is None else out
+    _check(_collab_mask(ctx.h, key.h, _ptr(w), _ptr(kappa), count, _ptr(out), _stream(stream)), "pc2_collab_mask")
+    return out
+
+
+def collab_edge_encrypt(ctx: Context, key: Key, ow, count: int, seed: int, stream_id: int, e0: int = 0, out=None,
+                        stream=None):
+    out = empty_tiled(count, key.limbs, ow.device) if out is None else out
+    _check(_collab_edge_encrypt(ctx.h, key.h, _ptr(ow), count, seed, stream_id, e0, _ptr(out), _stream(stream)),
+           "pc2_collab_edge_encrypt")
+    return out
+
+
+def collab_master_encrypt(ctx: Context, key: Key, w, kappa, cp, count: int, seed: int, stream_id: int, e0: int = 0,
+                          out=None, stream=None):
+    out = empty_tiled(count, 2 * key.limbs, w.device) if out is None else out
+    _check(_collab_master_encrypt(ctx.h, key.h, _ptr(w), _ptr(kappa), _ptr(cp), count, seed, stream_id, e0, _ptr(out),
+                                  _stream(stream)), "pc2_collab_master_encrypt")
+    return out
+
+
+def collab_edge_reduce(ctx: Context, key: Key, ct, count: int, out=None, stream=None):
+    out = empty_tiled(count, key.limbs, ct.device) if out is None else out
+    _check(_collab_edge_reduce(ctx.h, key.h, _ptr(ct), count, _ptr(out), _stream(stream)), "pc2_collab_edge_reduce")
+    return out
+
+
+def collab_master_decrypt(ctx: Context, key: Key, ct, cp, count: int, out=None, stream=None):
+    out = empty_tiled(count, key.limbs, ct.device) if out is None else out
+    _check(_collab_master_decrypt(ctx.h, key.h, _ptr(ct), _ptr(cp), count, _ptr(out), _stream(stream)),
+           "pc2_collab_master_decrypt")
+    return out
