@@ -36,6 +36,9 @@ UNIT = "Paillier enc+dec ops/s"
 # of this build (2^17 elements: 10.77 GB + 4.27 GB), scaled to a launch by the
 # elements it processes; None once the kernel changes.
 ENC_DRAM_BYTES_PER_ELEM = 114776
+# DRAM bytes (read + write) per element of one k_modexp_tc launch from an ncu
+# capture of the current build; None until one is taken.
+TC_DRAM_BYTES_PER_ELEM = None
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
 IMAD_PER_CLK_SM = 64   # nominal 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
 CPU_PER_GROUP = 4      # CPU sample: 16 x 4 encryptions, 16-group products, 4 decryptions per step
@@ -779,6 +782,22 @@ def run_gpu(args):
         pc2.set_engine(ctx, args.engine)
         assert ctx.status() == 0
 
+    # stage times of the tensor-core path (CUDA events recorded by the library
+    # on this stream around each of its launches), one encryption of the batch
+    # and one decryption of the aggregates
+    stages = None
+    if rank == 0 and args.engine != 0:
+        pc2.set_timing(ctx, True)
+        flush.zero_()
+        pc2.encrypt(ctx, key, dm, SEED, STREAM, e0=e0, out=ct)
+        st_enc = pc2.stage_ms(ctx)
+        flush.zero_()
+        pc2.decrypt(ctx, key, agg, per_group, out=dec)
+        st_dec = pc2.stage_ms(ctx)
+        pc2.set_timing(ctx, False)
+        stages = {"encrypt": dict(zip(["setup", "power_p2", "power_q2", "finish"], st_enc)),
+                  "decrypt_2p16": dict(zip(["setup", "power_p2", "power_q2", "finish"], st_dec))}
+
     # decryption of the whole batch (all 2^20 ciphertexts), outside the step
     dec_full_ms = None
     if rank == 0:
@@ -821,8 +840,8 @@ def run_gpu(args):
     if probe:
         peak = probe["product_peak_per_s"] / 1e12
         lohi = probe["lo_hi_product"]["per_s"] / 1e12
-        for name, prods, cnt, t in (("k_enc_crt", prod_enc, N_PLAIN, enc_ms), ("k_dec_crt (2^16 aggregates)", prod_dec,
-                                    per_group, dec_ms), ("k_dec_crt (2^20 ciphertexts)", prod_dec, N_PLAIN, dec_full_ms),
+        for name, prods, cnt, t in (("encrypt (2^20)", prod_enc, N_PLAIN, enc_ms), ("decrypt (2^16 aggregates)", prod_dec,
+                                    per_group, dec_ms), ("decrypt (2^20 ciphertexts)", prod_dec, N_PLAIN, dec_full_ms),
                                     ("k_hom_sum", prod_sum, per_group, sum_ms)):
             a = prods * cnt / (t / 1e3) / 1e12
             fr[name] = {"achieved_tprod_s": a, "frac_of_measured_peak": a / peak, "frac_of_lo_hi_rate": a / lohi}
@@ -840,6 +859,33 @@ def run_gpu(args):
                 "frac": a / nominal_imad, "peak_note": "nominal (probe skipped): %d SMs x %d IMAD/clk x %.0f MHz" % (
                     sms, IMAD_PER_CLK_SM, sm_max)}
     roof["traffic"] = ENC_DRAM_BYTES_PER_ELEM * N_PLAIN if ENC_DRAM_BYTES_PER_ELEM else None
+    if stages and probe:
+        # the dominant kernel of the tensor-core path: the full-width powers
+        # (k_modexp_tc).  Its integer pipe forms T = a b (a squaring's cross
+        # products and squares: L (L + 1) / 2 word products; a general
+        # product: L^2); its tensor cores the reduction's contractions
+        # (73728 bf16 MACs per product and element).
+        sq, mu, lb = pc2.power_counts(key, 0)
+        imad_prod = sq * lb * (lb + 1) // 2 + mu * lb * lb
+        t_pow = (stages["encrypt"]["power_p2"] + stages["encrypt"]["power_q2"]) / 1e3
+        ach = imad_prod * N_PLAIN / t_pow / 1e12
+        lohi = probe["lo_hi_product"]["per_s"] / 1e12
+        tflops = 2.0 * 73728 * (sq + mu) * N_PLAIN / t_pow / 1e12
+        cios_eq = (sq + mu) * (2 * lb * lb + lb) * N_PLAIN / t_pow / 1e12
+        peak_tc = peaks.get("bf16_tflops")
+        roof = {"bound": "alu", "kernel": "k_modexp_tc", "achieved": ach, "peak": lohi,
+                "unit": "T word products/s (integer pipe: mad.lo.cc + madc.hi.cc per 32x32->64 product)",
+                "frac": ach / lohi, "traffic": TC_DRAM_BYTES_PER_ELEM * N_PLAIN if TC_DRAM_BYTES_PER_ELEM else None,
+                "peak_note": "measured: pc2_probe_mul lo_hi_product rate (of measured), the instruction pattern of the "
+                             "kernel's products; both launches of the encryption's powers (mod p^2, q^2), CUDA "
+                             "events on the launching stream",
+                "per_element": {"squarings": sq, "products": mu, "limbs": lb, "integer_pipe_word_products": imad_prod,
+                                "tensor_macs": 73728 * (sq + mu)},
+                "tensor": {"achieved_tflops": tflops, "peak_tflops": peak_tc,
+                           "frac": tflops / peak_tc if peak_tc else None, "peak_note": "MEASURED_PEAKS.json bf16_tflops"},
+                "cios_equivalent": {"achieved": cios_eq, "unit": "T word products/s (2 L^2 + L per Montgomery product)",
+                                    "frac_of_mad_wide_peak": cios_eq / (probe["product_peak_per_s"] / 1e12)},
+                "launches_s": t_pow}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -855,6 +901,7 @@ def run_gpu(args):
                    "dec_montmuls_per_elem": dmm, "montmul_limbs": lb, "enc_imads_per_elem": imad_per_elem,
                    "enc_products_per_elem": prod_enc, "dec_products_per_elem": prod_dec,
                    "hom_sum_products_per_elem": prod_sum, "fractions": fr, "engine_ab": engine_ab,
+                   "tc_stages_ms": stages,
                    "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 16384,
                               0: "integer pipe", 1: "tensor cores"}[args.engine]},
         "multiplier_probe": probe,

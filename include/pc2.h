@@ -100,6 +100,19 @@ int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
 #define PC2_ENGINE_TC 1
 #define PC2_TC_MIN_COUNT 16384
 int pc2_ctx_set_engine(pc2_ctx* ctx, int engine);
+/* Stage timing of the tensor-core path (a measurement aid; the paper has no
+ * counterpart).  With timing on, each tensor-core encryption or decryption
+ * records CUDA events on its stream around its four launches, and
+ * pc2_ctx_stage_ms writes the last such call's times in milliseconds to
+ * h_ms[0..3]: set-up, power mod p^2, power mod q^2, finish (it waits for the
+ * last event).  PC2_EINVAL when no timed tensor-core call was made. */
+int pc2_ctx_set_timing(pc2_ctx* ctx, int on);
+int pc2_ctx_stage_ms(pc2_ctx* ctx, double* h_ms);
+/* Squarings and general products of the full-width powers of one key-owner
+ * encryption (op 0: the lifted route's powers by p and q, or the reduced
+ * exponents) or decryption (op 2: by p - 1 and q - 1), tables included, and
+ * the limbs of their modulus.  Keys up to 2048 bits. */
+int pc2_key_power_counts(const pc2_key* key, int op, long* squarings, long* multiplies, int* limbs);
 /* Autotuner: times every built lane count x split (on, off) x window
  * width (4..6) of key-owner encryption (ops bit 0) and/or decryption (bit 1)
  * on `count` elements (at most two resident waves of them) and records the

@@ -235,7 +235,9 @@ static int enc_crt(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, const 
     if (use_tc(ctx, count)) {
       auto K = tc_mods(key, &rc);
       if (!K) return rc;
-      return launch_enc_crt_tc(*P, *K, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0);
+      ctx->ev_recorded = ctx->timing;
+      return launch_enc_crt_tc(*P, *K, m64, mw, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, 0,
+                               ctx->timing ? ctx->ev : nullptr);
     }
   }
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
@@ -329,7 +331,9 @@ static int dec(pc2_ctx* ctx, const pc2_key* key, const uint32_t* ct, size_t coun
     if (use_tc(ctx, count)) {
       auto K = tc_mods(key, &rc);
       if (!K) return rc;
-      return launch_dec_crt_tc(*P, *K, ct, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base);
+      ctx->ev_recorded = ctx->timing;
+      return launch_dec_crt_tc(*P, *K, ct, count, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base,
+                               ctx->timing ? ctx->ev : nullptr);
     }
   }
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
@@ -496,6 +500,8 @@ void pc2_ctx_destroy(pc2_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->status) cudaFree(ctx->status);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -551,6 +557,75 @@ int pc2_ctx_set_engine(pc2_ctx* ctx, int engine) {
   if (!ctx || (engine != -1 && engine != PC2_ENGINE_IMAD && engine != PC2_ENGINE_TC)) return PC2_EINVAL;
   ctx->engine = engine;
   return PC2_OK;
+}
+
+int pc2_ctx_set_timing(pc2_ctx* ctx, int on) {
+  if (!ctx) return PC2_EINVAL;
+  if (on && !ctx->ev[0])
+    for (auto& e : ctx->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return PC2_ECUDA;
+  ctx->timing = on != 0;
+  ctx->ev_recorded = false;
+  return PC2_OK;
+}
+
+int pc2_ctx_stage_ms(pc2_ctx* ctx, double* h_ms) {
+  if (!ctx || !h_ms) return PC2_EINVAL;
+  if (!ctx->ev_recorded) return PC2_EINVAL;
+  if (cudaEventSynchronize(ctx->ev[4]) != cudaSuccess) return PC2_ECUDA;
+  for (int i = 0; i < 4; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) return PC2_ECUDA;
+    h_ms[i] = ms;
+  }
+  return PC2_OK;
+}
+
+int pc2_key_power_counts(const pc2_key* key, int op, long* squarings, long* multiplies, int* limbs) {
+  if (!key || !squarings || !multiplies || !limbs || (op != 0 && op != 2)) return PC2_EINVAL;
+  if (!key->priv) return PC2_EKEY;
+  auto count = [&](const auto& E, long& sq, long& mu) {
+    const int ntab = 1 << (E.w - 1);
+    if (ntab > 1) {
+      sq += 1;
+      mu += ntab - 1;
+    }
+    for (int i = 1; i < E.nsteps; ++i) {
+      sq += E.step[i] >> 8;
+      mu += ((E.step[i] & 0xffu) != 0u) ? 1 : 0;
+    }
+  };
+  *squarings = 0;
+  *multiplies = 0;
+  int rc = PC2_OK;
+  auto fill = [&](auto tag) -> int {
+    constexpr int Lh = decltype(tag)::value;
+    if (op == 0) {
+      auto P = enc_params<Lh>(key, &rc);
+      if (!P) return rc;
+      if constexpr (lift_route<Lh, 1>()) {
+        count(P->lp.e2, *squarings, *multiplies);
+        count(P->lq.e2, *squarings, *multiplies);
+      } else {
+        count(P->ep, *squarings, *multiplies);
+        count(P->eq, *squarings, *multiplies);
+      }
+    } else {
+      auto P = dec_params<Lh>(key, &rc);
+      if (!P) return rc;
+      count(P->ep, *squarings, *multiplies);
+      count(P->eq, *squarings, *multiplies);
+    }
+    *limbs = Lh;
+    return PC2_OK;
+  };
+  switch (key->Lh) {
+    case 8: return fill(std::integral_constant<int, 8>());
+    case 16: return fill(std::integral_constant<int, 16>());
+    case 32: return fill(std::integral_constant<int, 32>());
+    case 64: return fill(std::integral_constant<int, 64>());
+    default: return PC2_EUNSUPPORTED;
+  }
 }
 
 int pc2_autotune(pc2_ctx* ctx, const pc2_key* key, size_t count, int ops, pc2_stream_t stream, int* h_result) {

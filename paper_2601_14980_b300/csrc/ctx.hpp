@@ -22,6 +22,9 @@ struct pc2_ctx {
   int lanes = 0;          // 0 = automatic (tuned table, else fill heuristic)
   int split = 0;          // CRT halves in parallel: 0 automatic, 1 never, 2 whenever lanes > 1
   int engine = -1;        // full-width powers at 2048-bit n: -1 automatic, 0 integer pipe, 1 tensor cores
+  bool timing = false;    // record the stage boundaries of tensor-core calls
+  cudaEvent_t ev[5] = {};  // before set-up, after set-up, after power mod p^2, after power mod q^2, after finish
+  bool ev_recorded = false;
   // autotuned (lanes, window, split) per (op, limbs, ceil(log2 of the element count))
   std::mutex tune_mu;
   std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;

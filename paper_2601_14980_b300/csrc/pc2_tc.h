@@ -40,10 +40,13 @@ struct TcKeyMods {
 // Key-owner encryption / CRT decryption at 2048-bit n with the full-width
 // powers on the tensor cores; same arguments and results as launch_enc_crt /
 // launch_dec_crt.
+// ev (optional): five events recorded on `st` around the four launches
+// (before set-up, after set-up, after each power, after the finish).
 int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint64_t* m64, const uint32_t* mwide,
                       size_t count, uint32_t* out, ScratchFn scratch_fn, void* sctx, int* status, int sms,
-                      cudaStream_t st, size_t base);
+                      cudaStream_t st, size_t base, cudaEvent_t* ev);
 int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t* ct, size_t count, uint32_t* out,
-                      ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base);
+                      ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base,
+                      cudaEvent_t* ev);
 
 }  // namespace pc2

@@ -340,7 +340,7 @@ size_t power_scratch_words(int w, int sms) {
 
 int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint64_t* m64, const uint32_t* mwide,
                       size_t count, uint32_t* out, ScratchFn scratch_fn, void* sctx, int* status, int sms,
-                      cudaStream_t st, size_t base) {
+                      cudaStream_t st, size_t base, cudaEvent_t* ev) {
   constexpr int Lh = 64;
   const size_t smem = (size_t)Lh * kThreads * 4;
   auto pre = k_enc_tc_pre<Lh>;
@@ -361,17 +361,23 @@ int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint6
   uint32_t* sp = scratch;
   uint32_t* sq = scratch + vec;
   uint32_t* ws = scratch + 2 * vec;
+  if (ev) cudaEventRecord(ev[0], st);
   pre<<<gpre, kThreads, smem, st>>>(P, count, sp, sq, ws, tabw);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
+  if (ev) cudaEventRecord(ev[1], st);
   int rc = launch_power(K.p2, P.lp.e2, sp, count, ws, work, status, sms, st);
+  if (ev) cudaEventRecord(ev[2], st);
   if (rc == PC2_OK) rc = launch_power(K.q2, P.lq.e2, sq, count, ws, work, status, sms, st);
+  if (ev) cudaEventRecord(ev[3], st);
   if (rc != PC2_OK) return rc;
   post<<<gpost, kThreads, 0, st>>>(P, m64, mwide, count, sp, sq, out, ws, status, base);
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
 int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t* ct, size_t count, uint32_t* out,
-                      ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base) {
+                      ScratchFn scratch_fn, void* sctx, int* status, int sms, cudaStream_t st, size_t base,
+                      cudaEvent_t* ev) {
   constexpr int Lh = 64;
   auto pre = k_dec_tc_pre<Lh>;
   auto post = k_dec_tc_post<Lh>;
@@ -389,12 +395,17 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
   uint32_t* sp = scratch;
   uint32_t* sq = scratch + vec;
   uint32_t* ws = scratch + 2 * vec;
+  if (ev) cudaEventRecord(ev[0], st);
   pre<<<gpre, kThreads, 0, st>>>(P, ct, count, sp, sq, ws, base);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
+  if (ev) cudaEventRecord(ev[1], st);
   int rc = launch_power(K.p2, P.ep, sp, count, ws, work, status, sms, st);
+  if (ev) cudaEventRecord(ev[2], st);
   if (rc == PC2_OK) rc = launch_power(K.q2, P.eq, sq, count, ws, work, status, sms, st);
+  if (ev) cudaEventRecord(ev[3], st);
   if (rc != PC2_OK) return rc;
   post<<<gpost, kThreads, 0, st>>>(P, sp, sq, count, out, ws, base);
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 

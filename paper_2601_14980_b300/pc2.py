@@ -480,6 +480,30 @@ def set_engine(ctx: Context, engine: int):
     _check(_set_engine(ctx.h, engine), "pc2_ctx_set_engine")
 
 
+_set_timing = _sig("pc2_ctx_set_timing", [_vp, _i])
+_stage_ms = _sig("pc2_ctx_stage_ms", [_vp, ctypes.POINTER(ctypes.c_double)])
+_power_counts = _sig("pc2_key_power_counts", [_vp, _i, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                              ctypes.POINTER(_i)])
+
+
+def set_timing(ctx: Context, on: bool):
+    _check(_set_timing(ctx.h, int(on)), "pc2_ctx_set_timing")
+
+
+def stage_ms(ctx: Context) -> list:
+    """[set-up, power mod p^2, power mod q^2, finish] of the last timed tensor-core call (ms)."""
+    out = (ctypes.c_double * 4)()
+    _check(_stage_ms(ctx.h, out), "pc2_ctx_stage_ms")
+    return list(out)
+
+
+def power_counts(key: Key, op: int) -> tuple:
+    """(squarings, products, limbs) of the full-width powers of one element's op (0 encrypt, 2 decrypt)."""
+    sq, mu, lb = ctypes.c_long(), ctypes.c_long(), _i()
+    _check(_power_counts(key.h, op, ctypes.byref(sq), ctypes.byref(mu), ctypes.byref(lb)), "pc2_key_power_counts")
+    return sq.value, mu.value, lb.value
+
+
 def set_split(ctx: Context, mode: int):
     """CRT halves in parallel: 0 automatic, 1 never, 2 always."""
     _check(_ctx_set_split(ctx.h, mode), "pc2_ctx_set_split")
