@@ -204,11 +204,15 @@ static int with_n2_lanes(pc2_ctx* ctx, size_t count, Fn fn) {
 // The tensor-core blocks of p^2 and q^2 (2048-bit keys), cached per key.
 static std::shared_ptr<TcKeyMods> tc_mods(const pc2_key* key, int* rc) {
   return cached<TcKeyMods>(key, KIND_TC, 0, [&](TcKeyMods& K) {
-    uint32_t w[tc::kL];
-    mul(key->p, key->p).to_words(w, tc::kL);
-    if (!tc::build_mod(w, K.p2)) return PC2_EKEY;
-    mul(key->q, key->q).to_words(w, tc::kL);
-    if (!tc::build_mod(w, K.q2)) return PC2_EKEY;
+    uint32_t w[64];
+    mul(key->p, key->p).to_words(w, 64);
+    if (!tc::build_mod<64>(w, K.p2)) return PC2_EKEY;
+    mul(key->q, key->q).to_words(w, 64);
+    if (!tc::build_mod<64>(w, K.q2)) return PC2_EKEY;
+    key->p.to_words(w, 32);
+    if (!tc::build_mod<32>(w, K.p)) return PC2_EKEY;
+    key->q.to_words(w, 32);
+    if (!tc::build_mod<32>(w, K.q)) return PC2_EKEY;
     return PC2_OK;
   }, rc);
 }

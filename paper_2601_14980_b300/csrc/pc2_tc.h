@@ -13,28 +13,29 @@
 namespace pc2 {
 namespace tc {
 
-constexpr int kL = 64;        // limbs of the modulus (2048 bits)
-constexpr int kB1Rows = 256;  // Toeplitz(N') slice rows: output columns 0..255
-constexpr int kB2Rows = 272;  // Toeplitz(N) slice rows: output columns 16 s .. 16 s + 271
-
-// A modulus N (64 words) with its two Toeplitz slices (bf16 bits, K-major,
-// no swizzle: K-block kb of 8 columns is a [rows x 8] row-major slab).
+// A modulus N of L words (L = 32 or 64) with its two Toeplitz slices (bf16
+// bits, K-major, no swizzle: K-block kb of 8 columns is a [rows x 8]
+// row-major slab).
+template <int L>
 struct alignas(16) Mod {
-  uint32_t n[kL];
-  uint16_t b1[kB1Rows * 16];  // digits of N' = -N^-1 mod 2^2048
-  uint16_t b2[kB2Rows * 16];  // digits of N
-  uint32_t np0;               // -N^-1 mod 2^32
+  uint32_t n[L];
+  uint16_t b1[4 * L * 16];        // digits of N' = -N^-1 mod 2^(32 L); rows 0 .. 4L-1
+  uint16_t b2[(4 * L + 16) * 16];  // digits of N; rows 0 .. 4L+15
+  uint32_t np0;                   // -N^-1 mod 2^32
   uint32_t pad_[3];
 };
 
 // Builds the block of an odd N (host).  False for an even N.
-bool build_mod(const uint32_t* n64, Mod& M);
+template <int L>
+bool build_mod(const uint32_t* n, Mod<L>& M);
 
 }  // namespace tc
 
-// The blocks of p^2 and q^2 of a 2048-bit key.
+// The blocks of p^2 and q^2 (64 words) and of p and q (32 words) of a
+// 2048-bit key.
 struct TcKeyMods {
-  tc::Mod p2, q2;
+  tc::Mod<64> p2, q2;
+  tc::Mod<32> p, q;
 };
 
 // Key-owner encryption / CRT decryption at 2048-bit n with the full-width

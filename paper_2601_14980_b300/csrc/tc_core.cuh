@@ -15,8 +15,8 @@
 // accumulation of kind::f16 tcgen05.mma is exact.
 //
 // A CTA owns tiles of 128 elements (MMA M = 128, TMEM lane e = element e):
-// warps 0-3 hold one element per thread, warp 4 allocates 256 TMEM columns
-// and serves the MMAs.  One product a <- a b / R mod N:
+// warps 0-3 hold one element per thread, warp 4 allocates 4L TMEM columns
+// (L limbs, 4L digits) and serves the MMAs.  Below for L = 64.  One product a <- a b / R mod N:
 //   1. warps 0-3: T = a b by rows on the integer pipe (a in registers, b's
 //      word i read from shared memory before row i); each finished low word
 //      of T is written as four bf16 digits into the A tile;
@@ -31,7 +31,8 @@
 // a fixed operand costs one small slice (8 KB for N', 8.5 KB for N), and the
 // A tile (64 KB) also holds each element's operand b: word i sits in the
 // first four bytes of the 8-byte slot that T word i overwrites after row i.
-// Shared memory per CTA: 81 KB; two CTAs per SM (2 x 256 TMEM columns).
+// Shared memory per CTA: 81 KB at L = 64 (two CTAs per SM, 2 x 256 TMEM
+// columns), 41 KB at L = 32 (three CTAs per SM, 3 x 128 columns).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,15 +45,9 @@
 namespace pc2 {
 namespace tc {
 
-constexpr int kD = 4 * kL;           // 8-bit digits per operand
 constexpr int kTileE = 128;          // elements per tile (MMA M)
 constexpr int kThreads = 160;        // warps 0-3 compute, warp 4 serves the MMAs
 constexpr int kSlab = kTileE * 16;   // bytes of one 8-digit K-block of the A tile
-constexpr int kAbytes = (kD / 8) * kSlab;   // 64 KB
-constexpr int kB1bytes = kB1Rows * 32;      // 8 KB
-constexpr int kB2bytes = kB2Rows * 32;      // 8.5 KB
-constexpr int kSmem = kAbytes + kB1bytes + kB2bytes + 64;
-constexpr uint32_t kTmemCols = 256;
 constexpr long kSpin = 1L << 20;     // bounded waits (a tile's MMAs take microseconds)
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -133,7 +128,39 @@ struct Smem {
   volatile uint32_t* cmd;   // 1: another product follows, 0: stop
   uint32_t* tmem_slot;
 };
-__device__ __forceinline__ Smem smem_layout(uint8_t* base) {
+// Per-thread state of the compute side.
+struct State {
+  uint32_t phase;
+  bool ok;
+};
+
+// Result of the product phase: t = T_hi (words 64..127 of T), the low words
+// already in the A tile as digits; nz = (T_lo != 0); top = words 62, 63 of T.
+struct Prod {
+  uint32_t nz, top0, top1;
+};
+
+// Compute warps: tells warp 4 that no product follows (all compute threads call it once).
+__device__ __forceinline__ void stop(const Smem& s) {
+  if (threadIdx.x == 0) *s.cmd = 0u;
+  bar_arrive1();
+}
+
+// The L-limb product (L = 32 or 64): digits, tile and TMEM sizes, and every
+// step that depends on them.
+template <int L>
+struct Core {
+  static constexpr int kL = L;
+  static constexpr int kD = 4 * L;              // 8-bit digits per operand
+  static constexpr int kB1Rows = kD;            // Toeplitz(N') slice rows: output columns 0 .. kD-1
+  static constexpr int kB2Rows = kD + 16;       // Toeplitz(N) slice rows: output columns 16 s .. 16 s + kD + 15
+  static constexpr int kAbytes = (kD / 8) * kSlab;
+  static constexpr int kB1bytes = kB1Rows * 32;
+  static constexpr int kB2bytes = kB2Rows * 32;
+  static constexpr int kSmem = kAbytes + kB1bytes + kB2bytes + 64;
+  static constexpr uint32_t kTmemCols = kD;     // a power of two for L = 32, 64
+
+static __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   Smem s;
   s.A = base;
   s.B1 = base + kAbytes;
@@ -145,8 +172,8 @@ __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
 }
 
 // Start of the kernel (all threads): the Toeplitz slices into shared memory,
-// the barrier, 256 TMEM columns.  Returns the TMEM base address.
-__device__ __forceinline__ uint32_t setup(const Smem& s, const Mod& M) {
+// the barrier, kD TMEM columns.  Returns the TMEM base address.
+static __device__ __forceinline__ uint32_t setup(const Smem& s, const Mod<L>& M) {
   const uint4* s1 = reinterpret_cast<const uint4*>(M.b1);
   const uint4* s2 = reinterpret_cast<const uint4*>(M.b2);
   for (int i = threadIdx.x; i < kB1bytes / 16; i += kThreads) reinterpret_cast<uint4*>(s.B1)[i] = s1[i];
@@ -169,7 +196,7 @@ __device__ __forceinline__ uint32_t setup(const Smem& s, const Mod& M) {
 }
 
 // End of the kernel (all threads): release the TMEM columns.
-__device__ __forceinline__ void teardown(uint32_t tmem) {
+static __device__ __forceinline__ void teardown(uint32_t tmem) {
   fence_before();
   __syncthreads();
   if ((threadIdx.x >> 5) == 4) {
@@ -179,66 +206,48 @@ __device__ __forceinline__ void teardown(uint32_t tmem) {
 }
 
 // Warp 4: issues the three MMA groups of every product until told to stop.
-__device__ __forceinline__ void serve(const Smem& s, uint32_t tmem) {
+static __device__ __forceinline__ void serve(const Smem& s, uint32_t tmem) {
   const bool leader = (threadIdx.x & 31) == 0;
   const uint32_t a_base = smem_addr(s.A), b1_base = smem_addr(s.B1), b2_base = smem_addr(s.B2);
   for (;;) {
     bar_sync1();
     if (*s.cmd == 0u) break;
     fence_after();
-    // m-columns: slice s adds A[:, 16s..16s+15] x B1[0..255-16s] into columns 16s..255
+    // m-columns: slice s adds A[:, 16s..16s+15] x B1[0..kD-1-16s] into columns 16s..kD-1
     if (leader) {
       for (int k = 0; k < kD / 16; ++k)
         mma_bf16(tmem + 16 * k, sdesc(a_base + 2 * k * kSlab, kSlab, 128), sdesc(b1_base, kB1Rows * 16, 128),
-                 idesc_bf16(256 - 16 * k), k > 0);
+                 idesc_bf16(kD - 16 * k), k > 0);
       mma_commit(s.bar);
     }
     __syncwarp();
-    // columns 256..511 of m N into TMEM columns 0..255 (slice 15 first: it covers them all)
+    // columns kD..2kD-1 of m N into TMEM columns 0..kD-1 (the last slice first: it covers them all)
     bar_sync1();
     fence_after();
     if (leader) {
       for (int k = kD / 16 - 1; k >= 0; --k)
         mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
-                 sdesc(b2_base + (256 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16 * k + 16), k != kD / 16 - 1);
+                 sdesc(b2_base + (kD - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16 * k + 16), k != kD / 16 - 1);
       mma_commit(s.bar);
     }
     __syncwarp();
-    // columns 240..255 of m N into TMEM columns 0..15
+    // columns kD-16..kD-1 of m N into TMEM columns 0..15
     bar_sync1();
     fence_after();
     if (leader) {
       for (int k = kD / 16 - 1; k >= 0; --k)
         mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
-                 sdesc(b2_base + (240 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16), k != kD / 16 - 1);
+                 sdesc(b2_base + (kD - 16 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16), k != kD / 16 - 1);
       mma_commit(s.bar);
     }
     __syncwarp();
   }
 }
 
-// Compute warps: tells warp 4 that no product follows (all compute threads call it once).
-__device__ __forceinline__ void stop(const Smem& s) {
-  if (threadIdx.x == 0) *s.cmd = 0u;
-  bar_arrive1();
-}
-
-// Per-thread state of the compute side.
-struct State {
-  uint32_t phase;
-  bool ok;
-};
-
-// Result of the product phase: t = T_hi (words 64..127 of T), the low words
-// already in the A tile as digits; nz = (T_lo != 0); top = words 62, 63 of T.
-struct Prod {
-  uint32_t nz, top0, top1;
-};
-
 // Product phase of a general product, element e = threadIdx.x: T = a b with
 // b's words in their slots of the A tile (write_b_*), by rows on the integer
 // pipe; each finished low word of T becomes four digits in its slot.
-__device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
+static __device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
   const int e = threadIdx.x;
   uint8_t* A = s.A;
 #pragma unroll
@@ -267,7 +276,7 @@ __device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uint32_t (
 // positions 2i+1 .. i+64 (carry into i+65); positions up to 2i+2 are then
 // final, and those below 64 are parked in their slots of the A tile.
 template <int I>
-__device__ __forceinline__ void sqr_row(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
+static __device__ __forceinline__ void sqr_row(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
   mad_lo_cc(C[2 * I + 1], a[I], a[I + 1]);
 #pragma unroll
   for (int j = I + 2; j < kL; ++j) madc_lo_cc(C[I + j], a[I], a[j]);
@@ -281,7 +290,7 @@ __device__ __forceinline__ void sqr_row(uint32_t (&C)[2 * kL], const uint32_t (&
   if constexpr (2 * I + 2 < kL) *reinterpret_cast<uint32_t*>(A + slot_off(2 * I + 2, e)) = C[2 * I + 2];
 }
 template <int I, int END>
-__device__ __forceinline__ void sqr_rows(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
+static __device__ __forceinline__ void sqr_rows(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
   if constexpr (I < END) {
     sqr_row<I>(C, a, A, e);
     sqr_rows<I + 1, END>(C, a, A, e);
@@ -293,7 +302,7 @@ __device__ __forceinline__ void sqr_rows(uint32_t (&C)[2 * kL], const uint32_t (
 // unrolled, a in registers) and D = sum_i a_i^2 2^(64 i): 2080 word products
 // instead of 4096.  Finished words of C below 64 wait in their slots of the
 // A tile; one pass then doubles C, adds D and writes the low words' digits.
-__device__ __forceinline__ Prod product_sqr(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
+static __device__ __forceinline__ Prod product_sqr(const uint32_t (&a)[kL], uint32_t (&t)[kL], const Smem& s) {
   const int e = threadIdx.x;
   uint8_t* A = s.A;
   uint32_t C[2 * kL];
@@ -335,7 +344,7 @@ __device__ __forceinline__ Prod product_sqr(const uint32_t (&a)[kL], uint32_t (&
 
 // Reduction phase, element e = threadIdx.x: from T (t = T_hi, the low words'
 // digits in the A tile) to a = T / R mod N with the tensor cores.
-__device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], const Prod& pr, const Smem& s,
+static __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], const Prod& pr, const Smem& s,
                                        uint32_t tmem, const uint32_t* n, State& st) {
   const int e = threadIdx.x;
   const int warp = e >> 5;
@@ -348,11 +357,11 @@ __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], con
   st.ok = mbar_wait(s.bar, st.phase) && st.ok;
   st.phase ^= 1u;
   fence_after();
-  // 3. m = (sum_j C_j 256^j) mod R from columns 0..255; its digits into the A tile
+  // 3. m = (sum_j C_j 256^j) mod R from columns 0..kD-1; its digits into the A tile
   {
     uint64_t carry = 0;
 #pragma unroll 1
-    for (int ch = 0; ch < 16; ++ch) {
+    for (int ch = 0; ch < kD / 16; ++ch) {
       uint32_t r[16];
       tmem_ld16(lane_base + 16 * ch, r);
 #pragma unroll
@@ -370,12 +379,12 @@ __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], con
   st.ok = mbar_wait(s.bar, st.phase) && st.ok;
   st.phase ^= 1u;
   fence_after();
-  // 5a. t += Hi = sum_j C_{256+j} 256^j
-  uint32_t over = 0u;  // bit 2048 of the running sum
+  // 5a. t += Hi = sum_j C_{kD+j} 256^j
+  uint32_t over = 0u;  // bit 32 L of the running sum
   {
     uint64_t carry = 0;
 #pragma unroll
-    for (int ch = 0; ch < 16; ++ch) {
+    for (int ch = 0; ch < kD / 16; ++ch) {
       uint32_t r[16];
       tmem_ld16(lane_base + 16 * ch, r);
 #pragma unroll
@@ -393,9 +402,9 @@ __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], con
   st.ok = mbar_wait(s.bar, st.phase) && st.ok;
   st.phase ^= 1u;
   fence_after();
-  // 5b. carry out of the low half: T_lo + Lo = c R, Lo = sum_{j<256} C_j 256^j.
+  // 5b. carry out of the low half: T_lo + Lo = c R, Lo = sum_{j<kD} C_j 256^j.
   // Lo = F + c' R with F = (R - T_lo) mod R; c' = round((Lo - F) / R) from
-  // columns 248..255 and the top 64 bits of F (error below 2^-39).
+  // the top 8 columns and the top 64 bits of F (error below 2^-39).
   {
     uint32_t r[16];
     tmem_ld16(lane_base, r);
@@ -432,14 +441,14 @@ __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[kL], con
 
 
 // a <- a b / R mod N, b's words already in their slots (write_b_*).
-__device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
+static __device__ __forceinline__ void montmul(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
                                         State& st) {
   uint32_t t[kL];
   const Prod pr = product_rows(a, t, s);
   reduce(a, t, pr, s, tmem, n, st);
 }
 // a <- a^2 / R mod N (no operand slots needed).
-__device__ __forceinline__ void montsqr(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
+static __device__ __forceinline__ void montsqr(uint32_t (&a)[kL], const Smem& s, uint32_t tmem, const uint32_t* n,
                                         State& st) {
   uint32_t t[kL];
   const Prod pr = product_sqr(a, t, s);
@@ -447,16 +456,18 @@ __device__ __forceinline__ void montsqr(uint32_t (&a)[kL], const Smem& s, uint32
 }
 
 // b = the thread's own a (a squaring).
-__device__ __forceinline__ void write_b_self(const Smem& s, const uint32_t (&a)[kL]) {
+static __device__ __forceinline__ void write_b_self(const Smem& s, const uint32_t (&a)[kL]) {
 #pragma unroll
   for (int j = 0; j < kL; ++j) *reinterpret_cast<uint32_t*>(s.A + slot_off(j, threadIdx.x)) = a[j];
 }
 // b = word j at src[j * stride] (a table entry in global memory).
-__device__ __forceinline__ void write_b_global(const Smem& s, const uint32_t* src, size_t stride) {
+static __device__ __forceinline__ void write_b_global(const Smem& s, const uint32_t* src, size_t stride) {
 #pragma unroll 8
   for (int j = 0; j < kL; ++j)
     *reinterpret_cast<uint32_t*>(s.A + slot_off(j, threadIdx.x)) = src[(size_t)j * stride];
 }
+
+};
 
 }  // namespace tc
 }  // namespace pc2

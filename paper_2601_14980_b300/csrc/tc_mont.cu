@@ -15,10 +15,11 @@
 
 namespace {
 
-constexpr int kL = pc2::tc::kL;
+constexpr int kL = 64;
+using Core = pc2::tc::Core<kL>;
 
 struct alignas(16) SqrParams {
-  pc2::tc::Mod m;
+  pc2::tc::Mod<kL> m;
 };
 
 __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
@@ -26,10 +27,10 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
                   uint32_t* __restrict__ y, int* status) {
   namespace tc = pc2::tc;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const tc::Smem s = tc::smem_layout(smem);
-  const uint32_t tmem = tc::setup(s, P.m);
+  const tc::Smem s = Core::smem_layout(smem);
+  const uint32_t tmem = Core::setup(s, P.m);
   if ((threadIdx.x >> 5) == 4) {
-    tc::serve(s, tmem);
+    Core::serve(s, tmem);
   } else {
     tc::State st{0u, true};
     const size_t ntiles = (count + tc::kTileE - 1) / tc::kTileE;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
 #pragma unroll
       for (int j = 0; j < kL; ++j) a[j] = x[pc2::tiled_index(g, j, kL)];
       for (int it = 0; it < nsq; ++it) {
-        tc::montsqr(a, s, tmem, P.m.n, st);
+        Core::montsqr(a, s, tmem, P.m.n, st);
       }
       if (valid) {
 #pragma unroll
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
     tc::stop(s);
     if (!st.ok && status) atomicOr(status, PC2_ST_TIMEOUT);
   }
-  tc::teardown(tmem);
+  Core::teardown(tmem);
 }
 
 // ------------------------------------------------------------------ the integer-pipe kernel
@@ -92,15 +93,15 @@ extern "C" int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const 
   if (engine != PC2_ENGINE_IMAD && engine != PC2_ENGINE_TC) return PC2_EINVAL;
   if (!count) return PC2_OK;
   static thread_local SqrParams P;  // 17 KB: kept off the stack
-  if (!pc2::tc::build_mod(h_n, P.m)) return PC2_EINVAL;
+  if (!pc2::tc::build_mod<kL>(h_n, P.m)) return PC2_EINVAL;
   const cudaStream_t st = (cudaStream_t)stream;
   if (engine == PC2_ENGINE_TC) {
-    if (cudaFuncSetAttribute(k_mont_sqr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, pc2::tc::kSmem) !=
+    if (cudaFuncSetAttribute(k_mont_sqr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, Core::kSmem) !=
         cudaSuccess)
       return PC2_ECUDA;
     const size_t tiles = (count + pc2::tc::kTileE - 1) / pc2::tc::kTileE;
     const size_t grid = tiles < (size_t)(2 * ctx->sms) ? tiles : (size_t)(2 * ctx->sms);
-    k_mont_sqr_tc<<<(unsigned)grid, pc2::tc::kThreads, pc2::tc::kSmem, st>>>(P, d_x, count, nsq, d_y, ctx->status);
+    k_mont_sqr_tc<<<(unsigned)grid, pc2::tc::kThreads, Core::kSmem, st>>>(P, d_x, count, nsq, d_y, ctx->status);
   } else {
     const size_t smem = (size_t)kL * kImadThreads * 4;
     if (cudaFuncSetAttribute(k_mont_sqr_imad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -2,11 +2,11 @@
 // with the full-width powers on the tensor-core Montgomery product
 // (tc_core.cuh).
 //
-// Each operation runs as three launches:
-//   pre   (integer pipe) the per-element set-up of both CRT halves: for
-//         encryption the lifted route's half-width power
-//         s = r^(h' mod (h-1)) mod h and its lift s R mod h^2; for decryption
-//         c R mod h^2;
+// Each operation runs as set-up, powers and finish:
+//   pre   the per-element set-up of both CRT halves: for encryption r R_h
+//         mod h (integer pipe), the lifted route's half-width power
+//         s = r^(h' mod (h-1)) mod h (tensor cores, 32 limbs) and the lift
+//         s R mod h^2 (integer pipe); for decryption c R mod h^2;
 //   power (tensor cores) x <- x^E in the Montgomery domain mod h^2 for all
 //         elements, E = h (encryption, r^n = s^h mod h^2) or h - 1
 //         (decryption), by the same sliding-window schedule as the one-kernel
@@ -26,24 +26,31 @@
 namespace pc2 {
 
 // ------------------------------------------------------------------ the power on the tensor cores
+template <int L>
 struct TcExpParams {
-  tc::Mod m;
+  tc::Mod<L> m;
   Sched<kMaxSchedHalf> e;
 };
-static_assert(sizeof(TcExpParams) + 256 <= 32764, "parameter block too large");
+static_assert(sizeof(TcExpParams<64>) + 256 <= 32764, "parameter block too large");
 
-// x <- x^E (Montgomery domain, 64 words, tiled, in place).  tabs: per CTA
-// (2^(w-1) + 1) entries of 64 words x 128 elements (odd powers, then x^2).
-__global__ void __launch_bounds__(tc::kThreads, 2)
-    k_modexp_tc(const __grid_constant__ TcExpParams P, uint32_t* __restrict__ xy, size_t count,
+// Resident CTAs per SM of the power kernel: two at 64 limbs (registers and
+// the 64 KB A tile), three at 32 limbs.
+template <int L>
+constexpr int tc_ctas() { return L == 64 ? 2 : 3; }
+
+// x <- x^E (Montgomery domain, L words, tiled, in place).  tabs: per CTA
+// (2^(w-1) + 1) entries of L words x 128 elements (odd powers, then x^2).
+template <int L>
+__global__ void __launch_bounds__(tc::kThreads, tc_ctas<L>())
+    k_modexp_tc(const __grid_constant__ TcExpParams<L> P, uint32_t* __restrict__ xy, size_t count,
                 uint32_t* __restrict__ tabs, int* status) {
+  using Core = tc::Core<L>;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const tc::Smem s = tc::smem_layout(smem);
-  const uint32_t tmem = tc::setup(s, P.m);
+  const tc::Smem s = Core::smem_layout(smem);
+  const uint32_t tmem = Core::setup(s, P.m);
   if ((threadIdx.x >> 5) == 4) {
-    tc::serve(s, tmem);
+    Core::serve(s, tmem);
   } else {
-    constexpr int L = tc::kL;
     const int e = threadIdx.x;
     const int ntab = 1 << (P.e.w - 1);
     const size_t ts = tc::kTileE;  // words of one table entry are tc::kTileE apart
@@ -98,10 +105,10 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
           if (!more) break;
         }
         if (src < 0) {
-          tc::montsqr(a, s, tmem, P.m.n, st);
+          Core::montsqr(a, s, tmem, P.m.n, st);
         } else {
-          tc::write_b_global(s, entry(src), ts);
-          tc::montmul(a, s, tmem, P.m.n, st);
+          Core::write_b_global(s, entry(src), ts);
+          Core::montmul(a, s, tmem, P.m.n, st);
         }
         if (phase == 0) {  // x^2: keep it, restart from x
           uint32_t* t2 = entry(ntab);
@@ -132,61 +139,68 @@ __global__ void __launch_bounds__(tc::kThreads, 2)
     tc::stop(s);
     if (!st.ok && status) atomicOr(status, PC2_ST_TIMEOUT);
   }
-  tc::teardown(tmem);
+  Core::teardown(tmem);
 }
 
 // ------------------------------------------------------------------ encryption: set-up and finish
-// A = s R mod h^2 with s = r^(h' mod (h-1)) mod h from the raw draw X (the
-// lifted route of LiftConst, up to its power by h).
-template <int Lh>
-__device__ __forceinline__ void lift_prep(const ModConst<Lh>& M, const LiftConst<Lh>& H, const Col& X, const Col& A,
-                                          const Col& B, const Col& C, const Col& TT, const Col& tab, const Col& bsh,
-                                          const Grp<1>& g) {
-  constexpr int Lp = Lh / 2;
-  g_to_mont_2l(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, Lp, B, C, TT);  // x1 R_h
-  g_copy_param(B, H.h.r2, Lp);
-  g_mont(A, A, B, H.h.n, H.h.np, Lp, TT);                                  // x1 R_h^2
-  g_mont(C, X, B, H.h.n, H.h.np, Lp, TT);                                  // x0 R_h
-  g_addmod(A, A, C, H.h.n, Lp);                                            // r R_h mod h
-  __syncwarp();
-  {
-    uint32_t a[Lp];
-    load_seg(a, A, g);
-    run_modexp<Lp, 1>(a, H.e1, H.h.n, H.h.np, tab, bsh, g);              // s R_h
-    store_seg(A, a, g);
-  }
-  __syncwarp();
-  for (int j = Lp; j < Lh; ++j) A[j] = 0u;
-  g_copy_param(B, H.lift, Lh);
-  g_mont(A, A, B, M.n, M.np, Lh, TT);                                      // s R mod h^2
-}
-
+// Set-up 1: r R_h mod h for h = p, q (half width) from the raw draw X, the
+// start of the lifted route of LiftConst.
 template <int Lh>
 __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
-    k_enc_tc_pre(const __grid_constant__ EncCrtParams<Lh> P, size_t count, uint32_t* __restrict__ sp,
-                 uint32_t* __restrict__ sq, uint32_t* __restrict__ scratch, int tabw) {
-  extern __shared__ uint32_t bsh_all[];
-  const Grp<1> g;
+    k_enc_tc_pre1(const __grid_constant__ EncCrtParams<Lh> P, size_t count, uint32_t* __restrict__ rp,
+                  uint32_t* __restrict__ rq, uint32_t* __restrict__ scratch) {
+  constexpr int Lp = Lh / 2;
   const Layout ly(1);
-  const Col bsh{bsh_all + ly.gl, ly.G};
-  const Col tab = ly.slot(scratch, 0);
   const int SW = 2 * Lh + 4;
-  const Col X = ly.slot(scratch, tabw + 0 * SW), A = ly.slot(scratch, tabw + 1 * SW),
-            B = ly.slot(scratch, tabw + 2 * SW), C = ly.slot(scratch, tabw + 3 * SW),
-            TT = ly.slot(scratch, tabw + 4 * SW);
+  const Col X = ly.slot(scratch, 0 * SW), A = ly.slot(scratch, 1 * SW), B = ly.slot(scratch, 2 * SW),
+            C = ly.slot(scratch, 3 * SW), TT = ly.slot(scratch, 4 * SW);
   for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
     size_t e = base + ly.gl;
     const bool valid = e < count;
     if (!valid) e = count - 1;
     const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | P.kind) : P.stream;
     gen_r(X, P.seed, sid, P.e0 + e, Lh + 2, 2 * Lh);
-    lift_prep<Lh>(P.mp, P.lp, X, A, B, C, TT, tab, bsh, g);
-    if (valid)
-      for (int j = 0; j < Lh; ++j) sp[tiled_index(e, j, Lh)] = A[j];
-    lift_prep<Lh>(P.mq, P.lq, X, A, B, C, TT, tab, bsh, g);
-    if (valid)
-      for (int j = 0; j < Lh; ++j) sq[tiled_index(e, j, Lh)] = A[j];
-    __syncwarp();
+    for (int h = 0; h < 2; ++h) {
+      const LiftConst<Lh>& H = h ? P.lq : P.lp;
+      // r = x0 + x1 R_h: r R_h = x0 R_h + (x1 R_h) R_h mod h
+      g_to_mont_2l(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, Lp, B, C, TT);  // x1 R_h
+      g_copy_param(B, H.h.r2, Lp);
+      g_mont(A, A, B, H.h.n, H.h.np, Lp, TT);                                  // x1 R_h^2
+      g_mont(C, X, B, H.h.n, H.h.np, Lp, TT);                                  // x0 R_h
+      g_addmod(A, A, C, H.h.n, Lp);                                            // r R_h mod h
+      uint32_t* out = h ? rq : rp;
+      if (valid)
+        for (int j = 0; j < Lp; ++j) out[tiled_index(e, j, Lp)] = A[j];
+    }
+  }
+}
+
+// Set-up 2: s R mod h^2 from s R_h (the half-width power's result), the lift
+// of LiftConst: a Montgomery product with R_h^3 mod h^2.
+template <int Lh>
+__global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
+    k_enc_tc_pre2(const __grid_constant__ EncCrtParams<Lh> P, size_t count, const uint32_t* __restrict__ sp1,
+                  const uint32_t* __restrict__ sq1, uint32_t* __restrict__ sp, uint32_t* __restrict__ sq,
+                  uint32_t* __restrict__ scratch) {
+  constexpr int Lp = Lh / 2;
+  const Layout ly(1);
+  const int SW = 2 * Lh + 4;
+  const Col A = ly.slot(scratch, 0 * SW), B = ly.slot(scratch, 1 * SW), TT = ly.slot(scratch, 2 * SW);
+  for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
+    size_t e = base + ly.gl;
+    const bool valid = e < count;
+    if (!valid) e = count - 1;
+    for (int h = 0; h < 2; ++h) {
+      const ModConst<Lh>& M = h ? P.mq : P.mp;
+      const LiftConst<Lh>& H = h ? P.lq : P.lp;
+      const uint32_t* in = h ? sq1 : sp1;
+      for (int j = 0; j < Lh; ++j) A[j] = j < Lp ? in[tiled_index(e, j, Lp)] : 0u;
+      g_copy_param(B, H.lift, Lh);
+      g_mont(A, A, B, M.n, M.np, Lh, TT);  // s R mod h^2
+      uint32_t* out = h ? sq : sp;
+      if (valid)
+        for (int j = 0; j < Lh; ++j) out[tiled_index(e, j, Lh)] = A[j];
+    }
   }
 }
 
@@ -317,23 +331,27 @@ int grid_of(K kern, size_t smem, int sms) {
 }
 
 // The power of all `count` elements of x (in place) by schedule E mod M.
-int launch_power(const tc::Mod& M, const Sched<kMaxSchedHalf>& E, uint32_t* x, size_t count, uint32_t* tabs,
+template <int L>
+int launch_power(const tc::Mod<L>& M, const Sched<kMaxSchedHalf>& E, uint32_t* x, size_t count, uint32_t* tabs,
                  size_t tab_words, int* status, int sms, cudaStream_t st) {
-  static thread_local TcExpParams P;
+  static thread_local TcExpParams<L> P;
   P.m = M;
   P.e = E;
-  if (cudaFuncSetAttribute(k_modexp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem) != cudaSuccess)
+  auto kern = k_modexp_tc<L>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Core<L>::kSmem) != cudaSuccess)
     return PC2_ECUDA;
   const size_t tiles = (count + tc::kTileE - 1) / tc::kTileE;
-  size_t grid = tiles < (size_t)(2 * sms) ? tiles : (size_t)(2 * sms);
-  const size_t per_cta = (size_t)((1 << (E.w - 1)) + 1) * tc::kL * tc::kTileE;
+  const size_t cap = (size_t)tc_ctas<L>() * sms;
+  const size_t grid = tiles < cap ? tiles : cap;
+  const size_t per_cta = (size_t)((1 << (E.w - 1)) + 1) * L * tc::kTileE;
   if (grid * per_cta > tab_words) return PC2_ENOMEM;
-  k_modexp_tc<<<(unsigned)grid, tc::kThreads, tc::kSmem, st>>>(P, x, count, tabs, status);
+  kern<<<(unsigned)grid, tc::kThreads, tc::Core<L>::kSmem, st>>>(P, x, count, tabs, status);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
 
+template <int L>
 size_t power_scratch_words(int w, int sms) {
-  return (size_t)2 * sms * ((size_t)(1 << (w - 1)) + 1) * tc::kL * tc::kTileE;
+  return (size_t)tc_ctas<L>() * sms * ((size_t)(1 << (w - 1)) + 1) * L * tc::kTileE;
 }
 
 }  // namespace
@@ -341,33 +359,40 @@ size_t power_scratch_words(int w, int sms) {
 int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint64_t* m64, const uint32_t* mwide,
                       size_t count, uint32_t* out, ScratchFn scratch_fn, void* sctx, int* status, int sms,
                       cudaStream_t st, size_t base, cudaEvent_t* ev) {
-  constexpr int Lh = 64;
-  const size_t smem = (size_t)Lh * kThreads * 4;
-  auto pre = k_enc_tc_pre<Lh>;
+  constexpr int Lh = 64, Lp = 32;
+  auto pre1 = k_enc_tc_pre1<Lh>;
+  auto pre2 = k_enc_tc_pre2<Lh>;
   auto post = k_enc_tc_post<Lh>;
-  const int gpre = grid_of(pre, smem, sms), gpost = grid_of(post, 0, sms);
-  if (gpre < 0 || gpost < 0) return PC2_ECUDA;
-  const int wpre = P.lp.e1.w > P.lq.e1.w ? P.lp.e1.w : P.lq.e1.w;
-  const int tabw = (1 << (wpre - 1)) * Lh;
-  const size_t pre_words = ((size_t)tabw + 5 * (size_t)(2 * Lh + 4)) * (size_t)gpre * kThreads;
-  const size_t post_words = 8 * (size_t)(2 * Lh + 4) * (size_t)gpost * kThreads;
-  const int wpow = P.lp.e2.w > P.lq.e2.w ? P.lp.e2.w : P.lq.e2.w;
-  const size_t pow_words = power_scratch_words(wpow, sms);
-  size_t work = pre_words > post_words ? pre_words : post_words;
-  work = work > pow_words ? work : pow_words;
-  const size_t vec = ((count + 31) / 32) * 32 * Lh;  // one tiled 64-word vector
-  uint32_t* scratch = scratch_fn(sctx, (2 * vec + work) * 4);
+  const int g1 = grid_of(pre1, 0, sms), g2 = grid_of(pre2, 0, sms), gpost = grid_of(post, 0, sms);
+  if (g1 < 0 || g2 < 0 || gpost < 0) return PC2_ECUDA;
+  const size_t sw = 2 * Lh + 4;
+  const size_t glue = 8 * sw * (size_t)(g1 > gpost ? (g1 > g2 ? g1 : g2) : (gpost > g2 ? gpost : g2)) * kThreads;
+  const int w1 = P.lp.e1.w > P.lq.e1.w ? P.lp.e1.w : P.lq.e1.w;
+  const int w2 = P.lp.e2.w > P.lq.e2.w ? P.lp.e2.w : P.lq.e2.w;
+  const size_t pw1 = power_scratch_words<Lp>(w1, sms), pw2 = power_scratch_words<Lh>(w2, sms);
+  size_t work = glue > pw1 ? glue : pw1;
+  work = work > pw2 ? work : pw2;
+  const size_t tiles = (count + 31) / 32 * 32;
+  const size_t vec = tiles * Lh, vec1 = tiles * Lp;  // tiled vectors of 64 and 32 words
+  uint32_t* scratch = scratch_fn(sctx, (2 * vec + 2 * vec1 + work) * 4);
   if (!scratch) return PC2_ENOMEM;
   uint32_t* sp = scratch;
-  uint32_t* sq = scratch + vec;
-  uint32_t* ws = scratch + 2 * vec;
+  uint32_t* sq = sp + vec;
+  uint32_t* sp1 = sq + vec;
+  uint32_t* sq1 = sp1 + vec1;
+  uint32_t* ws = sq1 + vec1;
   if (ev) cudaEventRecord(ev[0], st);
-  pre<<<gpre, kThreads, smem, st>>>(P, count, sp, sq, ws, tabw);
+  pre1<<<g1, kThreads, 0, st>>>(P, count, sp1, sq1, ws);
+  if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
+  int rc = launch_power<Lp>(K.p, P.lp.e1, sp1, count, ws, work, status, sms, st);  // s R_h mod p
+  if (rc == PC2_OK) rc = launch_power<Lp>(K.q, P.lq.e1, sq1, count, ws, work, status, sms, st);
+  if (rc != PC2_OK) return rc;
+  pre2<<<g2, kThreads, 0, st>>>(P, count, sp1, sq1, sp, sq, ws);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
   if (ev) cudaEventRecord(ev[1], st);
-  int rc = launch_power(K.p2, P.lp.e2, sp, count, ws, work, status, sms, st);
+  rc = launch_power<Lh>(K.p2, P.lp.e2, sp, count, ws, work, status, sms, st);  // (r^n mod p^2) R
   if (ev) cudaEventRecord(ev[2], st);
-  if (rc == PC2_OK) rc = launch_power(K.q2, P.lq.e2, sq, count, ws, work, status, sms, st);
+  if (rc == PC2_OK) rc = launch_power<Lh>(K.q2, P.lq.e2, sq, count, ws, work, status, sms, st);
   if (ev) cudaEventRecord(ev[3], st);
   if (rc != PC2_OK) return rc;
   post<<<gpost, kThreads, 0, st>>>(P, m64, mwide, count, sp, sq, out, ws, status, base);
@@ -386,7 +411,7 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
   const size_t pre_words = 5 * (size_t)(2 * Lh + 4) * (size_t)gpre * kThreads;
   const size_t post_words = 7 * (size_t)(2 * Lh + 4) * (size_t)gpost * kThreads;
   const int wpow = P.ep.w > P.eq.w ? P.ep.w : P.eq.w;
-  const size_t pow_words = power_scratch_words(wpow, sms);
+  const size_t pow_words = power_scratch_words<Lh>(wpow, sms);
   size_t work = pre_words > post_words ? pre_words : post_words;
   work = work > pow_words ? work : pow_words;
   const size_t vec = ((count + 31) / 32) * 32 * Lh;
@@ -399,9 +424,9 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
   pre<<<gpre, kThreads, 0, st>>>(P, ct, count, sp, sq, ws, base);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
   if (ev) cudaEventRecord(ev[1], st);
-  int rc = launch_power(K.p2, P.ep, sp, count, ws, work, status, sms, st);
+  int rc = launch_power<Lh>(K.p2, P.ep, sp, count, ws, work, status, sms, st);
   if (ev) cudaEventRecord(ev[2], st);
-  if (rc == PC2_OK) rc = launch_power(K.q2, P.eq, sq, count, ws, work, status, sms, st);
+  if (rc == PC2_OK) rc = launch_power<Lh>(K.q2, P.eq, sq, count, ws, work, status, sms, st);
   if (ev) cudaEventRecord(ev[3], st);
   if (rc != PC2_OK) return rc;
   post<<<gpost, kThreads, 0, st>>>(P, sp, sq, count, out, ws, base);
@@ -420,23 +445,25 @@ uint16_t bf16_of_digit(uint32_t d) {
   return (uint16_t)(u >> 16);  // exact: d < 256 needs 8 significant bits
 }
 
-// Slice of the Toeplitz matrix of a 256-digit operand: row n, K column kk
-// holds digit n - kk when 0 <= n - kk < 256.
+// Slice of the Toeplitz matrix of a 4L-digit operand w: row n, K column kk
+// holds digit n - kk when 0 <= n - kk < 4L.
+template <int L>
 void toeplitz_slice(const uint32_t* w, int rows, uint16_t* out) {
   for (int n = 0; n < rows; ++n)
     for (int kk = 0; kk < 16; ++kk) {
       const int d = n - kk;
-      const uint32_t v = (d >= 0 && d < 4 * kL) ? (w[d / 4] >> (8 * (d % 4))) & 0xffu : 0u;
+      const uint32_t v = (d >= 0 && d < 4 * L) ? (w[d / 4] >> (8 * (d % 4))) & 0xffu : 0u;
       out[(kk / 8) * rows * 8 + n * 8 + (kk % 8)] = bf16_of_digit(v);
     }
 }
 
-// r = a b mod 2^(32 kL)
+// r = a b mod 2^(32 L)
+template <int L>
 void mullo(const uint32_t* a, const uint32_t* b, uint32_t* r) {
-  for (int j = 0; j < kL; ++j) r[j] = 0u;
-  for (int i = 0; i < kL; ++i) {
+  for (int j = 0; j < L; ++j) r[j] = 0u;
+  for (int i = 0; i < L; ++i) {
     uint64_t c = 0;
-    for (int j = 0; i + j < kL; ++j) {
+    for (int j = 0; i + j < L; ++j) {
       c += (uint64_t)a[i] * b[j] + r[i + j];
       r[i + j] = (uint32_t)c;
       c >>= 32;
@@ -446,37 +473,40 @@ void mullo(const uint32_t* a, const uint32_t* b, uint32_t* r) {
 
 }  // namespace
 
-bool build_mod(const uint32_t* n64, Mod& M) {
-  if (!(n64[0] & 1u)) return false;
-  std::memcpy(M.n, n64, sizeof(M.n));
-  // N^-1 mod 2^2048 by Newton's iteration x <- x (2 - N x), doubling the correct bits
-  uint32_t inv[kL] = {}, t[kL], u[kL];
+template <int L>
+bool build_mod(const uint32_t* n, Mod<L>& M) {
+  if (!(n[0] & 1u)) return false;
+  std::memcpy(M.n, n, sizeof(M.n));
+  // N^-1 mod 2^(32 L) by Newton's iteration x <- x (2 - N x), doubling the correct bits
+  uint32_t inv[L] = {}, t[L], u[L];
   uint32_t x0 = 1u;
-  for (int i = 0; i < 5; ++i) x0 *= 2u - n64[0] * x0;  // mod 2^32
+  for (int i = 0; i < 5; ++i) x0 *= 2u - n[0] * x0;  // mod 2^32
   inv[0] = x0;
   for (int it = 0; it < 6; ++it) {  // 32 -> 2048 correct bits
-    mullo(inv, n64, t);
-    uint64_t br = 0;  // u = 2 - t mod 2^2048
-    for (int j = 0; j < kL; ++j) {
-      const uint64_t s = j == 0 ? 2ull : 0ull, v = (uint64_t)t[j] + br;
-      u[j] = (uint32_t)(s - v);
-      br = s < v;
+    mullo<L>(inv, n, t);
+    uint64_t br = 0;  // u = 2 - t mod 2^(32 L)
+    for (int j = 0; j < L; ++j) {
+      const uint64_t s2 = j == 0 ? 2ull : 0ull, v = (uint64_t)t[j] + br;
+      u[j] = (uint32_t)(s2 - v);
+      br = s2 < v;
     }
-    mullo(inv, u, t);
+    mullo<L>(inv, u, t);
     std::memcpy(inv, t, sizeof(inv));
   }
-  uint32_t np[kL];  // N' = 2^2048 - N^-1
+  uint32_t np[L];  // N' = 2^(32 L) - N^-1
   uint64_t br = 0;
-  for (int j = 0; j < kL; ++j) {
+  for (int j = 0; j < L; ++j) {
     const uint64_t v = (uint64_t)inv[j] + br;
     np[j] = (uint32_t)(0ull - v);
     br = v != 0;
   }
   M.np0 = np[0];
-  toeplitz_slice(np, kB1Rows, M.b1);
-  toeplitz_slice(n64, kB2Rows, M.b2);
+  toeplitz_slice<L>(np, 4 * L, M.b1);
+  toeplitz_slice<L>(n, 4 * L + 16, M.b2);
   return true;
 }
+template bool build_mod<32>(const uint32_t*, Mod<32>&);
+template bool build_mod<64>(const uint32_t*, Mod<64>&);
 
 }  // namespace tc
 }  // namespace pc2
