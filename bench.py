@@ -902,7 +902,7 @@ def run_gpu(args):
                    "enc_products_per_elem": prod_enc, "dec_products_per_elem": prod_dec,
                    "hom_sum_products_per_elem": prod_sum, "fractions": fr, "engine_ab": engine_ab,
                    "tc_stages_ms": stages,
-                   "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 16384,
+                   "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 32768,
                               0: "integer pipe", 1: "tensor cores"}[args.engine]},
         "multiplier_probe": probe,
         "roofline": roof,

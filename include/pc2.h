@@ -98,7 +98,7 @@ int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
  * always use the integer pipe.  PC2_EINVAL for another value. */
 #define PC2_ENGINE_IMAD 0
 #define PC2_ENGINE_TC 1
-#define PC2_TC_MIN_COUNT 16384
+#define PC2_TC_MIN_COUNT 32768
 int pc2_ctx_set_engine(pc2_ctx* ctx, int engine);
 /* Stage timing of the tensor-core path (a measurement aid; the paper has no
  * counterpart).  With timing on, each tensor-core encryption or decryption
