@@ -483,7 +483,7 @@ PAPER_TABLE2_RTX4060 = {
 def run_tc_mont(dev, count: int = 1 << 20, nsq: int = 64, reps: int = 3):
     """The tensor-core experiment: nsq Montgomery squarings of `count`
     elements mod N = p^2 (2048 bits) of the benchmark's key, with the
-    reduction's contractions on tcgen05 (bf16 digits) vs the integer-pipe
+    reduction's contractions on tcgen05 (f16 digits) vs the integer-pipe
     CIOS product.  Inputs resident in device memory, CUDA events, mean of
     `reps` after one warm-up; both results compared word for word."""
     import torch
@@ -640,15 +640,18 @@ def run_hbm(dev, n: int = 1 << 27, n_dec: int = 1 << 24, reps: int = 5):
 def run_probe(dev) -> dict:
     """Measured rates of the 32-bit multiplies on this GPU (pc2_probe_mul):
     mad.lo, mad.hi, mad.wide (a whole 32x32->64 product), a product as
-    mad.lo + mad.hi, and the carry-chained rows of a 64-limb Montgomery
-    product at the encryption kernel's occupancy (3 CTAs of 128 per SM).
+    mad.lo + mad.hi, the carry-chained rows of a 64-limb Montgomery
+    product (the integer-pipe engine) and the same rows as wide products
+    with 64-bit adds (the tensor-core engine's integer half), both at 3 CTAs
+    of 128 per SM, and the FP64 add rate.
     Per SM and clock from clock64 inside the loops; per second from CUDA
     events around each launch (after one untimed warm-up launch)."""
     from paper_2601_14980_b300 import pc2
 
     kinds = [("mad_lo", pc2.PROBE_LO, 8, 40000), ("mad_hi", pc2.PROBE_HI, 8, 20000),
              ("mad_wide", pc2.PROBE_WIDE, 8, 20000), ("lo_hi_product", pc2.PROBE_LOHI, 8, 15000),
-             ("cios_row_64_limbs", pc2.PROBE_ROW, 3, 600)]
+             ("cios_row_64_limbs", pc2.PROBE_ROW, 3, 600), ("wide_row_64_limbs", pc2.PROBE_ROWW, 3, 600),
+             ("fp64_add", pc2.PROBE_DADD, 8, 2000)]
     out = {}
     clk = Clocks(dev)
     for name, kind, bps, iters in kinds:
@@ -787,16 +790,17 @@ def run_gpu(args):
     # and one decryption of the aggregates
     stages = None
     if rank == 0 and args.engine != 0:
+        def timed_stages(fn):
+            flush.zero_()
+            fn()
+            try:
+                return dict(zip(["setup", "power_p2", "power_q2", "finish"], pc2.stage_ms(ctx)))
+            except pc2.Pc2Error:    # the call ran on the integer-pipe engine (below its size threshold)
+                return None
         pc2.set_timing(ctx, True)
-        flush.zero_()
-        pc2.encrypt(ctx, key, dm, SEED, STREAM, e0=e0, out=ct)
-        st_enc = pc2.stage_ms(ctx)
-        flush.zero_()
-        pc2.decrypt(ctx, key, agg, per_group, out=dec)
-        st_dec = pc2.stage_ms(ctx)
+        stages = {"encrypt": timed_stages(lambda: pc2.encrypt(ctx, key, dm, SEED, STREAM, e0=e0, out=ct)),
+                  "decrypt_2p16": timed_stages(lambda: pc2.decrypt(ctx, key, agg, per_group, out=dec))}
         pc2.set_timing(ctx, False)
-        stages = {"encrypt": dict(zip(["setup", "power_p2", "power_q2", "finish"], st_enc)),
-                  "decrypt_2p16": dict(zip(["setup", "power_p2", "power_q2", "finish"], st_dec))}
 
     # decryption of the whole batch (all 2^20 ciphertexts), outside the step
     dec_full_ms = None
@@ -859,30 +863,32 @@ def run_gpu(args):
                 "frac": a / nominal_imad, "peak_note": "nominal (probe skipped): %d SMs x %d IMAD/clk x %.0f MHz" % (
                     sms, IMAD_PER_CLK_SM, sm_max)}
     roof["traffic"] = ENC_DRAM_BYTES_PER_ELEM * N_PLAIN if ENC_DRAM_BYTES_PER_ELEM else None
-    if stages and probe:
+    if stages and stages["encrypt"] and probe:
         # the dominant kernel of the tensor-core path: the full-width powers
         # (k_modexp_tc).  Its integer pipe forms T = a b (a squaring's cross
         # products and squares: L (L + 1) / 2 word products; a general
         # product: L^2); its tensor cores the reduction's contractions
-        # (73728 bf16 MACs per product and element).
+        # (73728 f16 MACs per product and element).
         sq, mu, lb = pc2.power_counts(key, 0)
         imad_prod = sq * lb * (lb + 1) // 2 + mu * lb * lb
         t_pow = (stages["encrypt"]["power_p2"] + stages["encrypt"]["power_q2"]) / 1e3
         ach = imad_prod * N_PLAIN / t_pow / 1e12
-        lohi = probe["lo_hi_product"]["per_s"] / 1e12
+        roww = probe["wide_row_64_limbs"]["per_s"] / 1e12
         tflops = 2.0 * 73728 * (sq + mu) * N_PLAIN / t_pow / 1e12
         cios_eq = (sq + mu) * (2 * lb * lb + lb) * N_PLAIN / t_pow / 1e12
         peak_tc = peaks.get("bf16_tflops")
-        roof = {"bound": "alu", "kernel": "k_modexp_tc", "achieved": ach, "peak": lohi,
-                "unit": "T word products/s (integer pipe: mad.lo.cc + madc.hi.cc per 32x32->64 product)",
-                "frac": ach / lohi, "traffic": TC_DRAM_BYTES_PER_ELEM * N_PLAIN if TC_DRAM_BYTES_PER_ELEM else None,
-                "peak_note": "measured: pc2_probe_mul lo_hi_product rate (of measured), the instruction pattern of the "
-                             "kernel's products; both launches of the encryption's powers (mod p^2, q^2), CUDA "
-                             "events on the launching stream",
+        roof = {"bound": "alu", "kernel": "k_modexp_tc", "achieved": ach, "peak": roww,
+                "unit": "T word products/s (integer pipe: one mad.wide.u32 and a 64-bit add per 32x32->64 product)",
+                "frac": ach / roww, "traffic": TC_DRAM_BYTES_PER_ELEM * N_PLAIN if TC_DRAM_BYTES_PER_ELEM else None,
+                "peak_note": "measured: pc2_probe_mul wide_row_64_limbs rate (of measured), 64-limb rows in the "
+                             "instruction pattern of the kernel's products; achieved over both launches of the "
+                             "encryption's powers (mod p^2, q^2), CUDA events on the launching stream",
+                "frac_of_mad_wide": ach / (probe["mad_wide"]["per_s"] / 1e12),
                 "per_element": {"squarings": sq, "products": mu, "limbs": lb, "integer_pipe_word_products": imad_prod,
                                 "tensor_macs": 73728 * (sq + mu)},
                 "tensor": {"achieved_tflops": tflops, "peak_tflops": peak_tc,
-                           "frac": tflops / peak_tc if peak_tc else None, "peak_note": "MEASURED_PEAKS.json bf16_tflops"},
+                           "frac": tflops / peak_tc if peak_tc else None,
+                           "peak_note": "MEASURED_PEAKS.json bf16_tflops (f16 and bf16 share the dense rate)"},
                 "cios_equivalent": {"achieved": cios_eq, "unit": "T word products/s (2 L^2 + L per Montgomery product)",
                                     "frac_of_mad_wide_peak": cios_eq / (probe["product_peak_per_s"] / 1e12)},
                 "launches_s": t_pow}
@@ -919,6 +925,14 @@ def run_gpu(args):
         "admm_full": None if args.no_admm_full else run_admm_full(dev),
         "tc_mont": None if args.no_tc else run_tc_mont(dev),
     }
+    if line["hbm"] and probe:
+        # the z/v update spends three IEEE double additions per element
+        # (v + x, a - kappa, a - z); against the measured FP64 add rate
+        zv = line["hbm"]["steps"]["zv_update"]
+        rate = probe["fp64_add"]["per_s"]
+        zv["fp64_adds_per_elem"] = 3
+        zv["fp64_frac"] = 3 * zv["elements"] / (zv["ms"] / 1e3) / rate
+        zv["fp64_add_peak_per_s"] = rate
     print(json.dumps(line))
     if dist: dist.destroy_process_group()
 

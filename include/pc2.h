@@ -105,7 +105,8 @@ int pc2_ctx_set_engine(pc2_ctx* ctx, int engine);
  * records CUDA events on its stream around its four launches, and
  * pc2_ctx_stage_ms writes the last such call's times in milliseconds to
  * h_ms[0..3]: set-up, power mod p^2, power mod q^2, finish (it waits for the
- * last event).  PC2_EINVAL when no timed tensor-core call was made. */
+ * last event).  PC2_EINVAL unless the context's last encryption or
+ * decryption ran, timed, on the tensor-core engine. */
 int pc2_ctx_set_timing(pc2_ctx* ctx, int on);
 int pc2_ctx_stage_ms(pc2_ctx* ctx, double* h_ms);
 /* Squarings and general products of the full-width powers of one key-owner
@@ -456,7 +457,7 @@ int pc2_collab_master_decrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* 
  * powers of Eq. (itq1) and Sec. III-C.  engine PC2_ENGINE_IMAD runs the
  * library's CIOS product on the integer pipe; PC2_ENGINE_TC computes the
  * product a a on the integer pipe and the reduction's two contractions with
- * the fixed modulus, m = (T mod R) N' mod R and m N, as bf16 tcgen05.mma
+ * the fixed modulus, m = (T mod R) N' mod R and m N, as f16 tcgen05.mma
  * over 8-bit digits (the paper's recasting of big-integer products as
  * low-bitwidth matrix operations, Alg. 2, done on B300's tensor cores).  Both
  * give the same integers.
@@ -479,8 +480,11 @@ int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const uint32_t* d
  *   PC2_PROBE_HI    mad.hi.u32 (high half)
  *   PC2_PROBE_WIDE  mad.wide.u32 (a whole 32x32->64 product, plus a 64-bit add)
  *   PC2_PROBE_LOHI  a 32x32->64 product as mad.lo + mad.hi
+ *   PC2_PROBE_DADD  add.rn.f64 (FP64 adds, the pipe of the z/v update)
  *   PC2_PROBE_ROW   the carry-chained rows of a 64-limb Montgomery product,
- *                   the instruction pattern of the library's product core
+ *                   the instruction pattern of the integer-pipe engine
+ *   PC2_PROBE_ROWW  the same rows as wide products with 64-bit adds, the
+ *                   pattern of the tensor-core engine's integer-pipe half
  * Launches blocks_per_sm x SMs CTAs of 128 threads (PC2_EINVAL when that
  * many cannot all be resident, or iters < 1); every thread runs `iters`
  * loop trips of independent accumulators.  Allocates its own small buffers
@@ -494,6 +498,8 @@ int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const uint32_t* d
 #define PC2_PROBE_WIDE 2
 #define PC2_PROBE_LOHI 3
 #define PC2_PROBE_ROW 4
+#define PC2_PROBE_DADD 5
+#define PC2_PROBE_ROWW 6
 int pc2_probe_mul(int device, int kind, int blocks_per_sm, int iters, pc2_stream_t stream, double* ops, double* ms,
                   double* cycles, int* sms);
 

@@ -846,6 +846,7 @@ static int encrypt_any(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, co
                        uint64_t seed, uint32_t stream, uint64_t e0, uint32_t* d_ct, pc2_stream_t cs, bool force_pub) {
   if (!ctx || !key || !d_ct || (!m64 && !mw)) return count ? PC2_EINVAL : PC2_OK;
   if (!count) return PC2_OK;
+  ctx->ev_recorded = false;  // set again only if this call runs on the tensor cores
   const cudaStream_t st = (cudaStream_t)cs;
   if (key->priv && !force_pub) {
 #define PC2_CALL_CRT(L) enc_crt<L>(ctx, key, m64, mw, count, seed, stream, e0, d_ct, st)
@@ -879,6 +880,7 @@ int pc2_decrypt(pc2_ctx* ctx, const pc2_key* key, const uint32_t* d_ct, size_t c
   if (!key->priv) return PC2_EKEY;
   if (!count) return PC2_OK;
   if (!d_ct || !d_m) return PC2_EINVAL;
+  ctx->ev_recorded = false;  // set again only if this call runs on the tensor cores
   const cudaStream_t st = (cudaStream_t)cstream;
 #define PC2_CALL_DEC(L) dec<L>(ctx, key, d_ct, count, d_m, st)
   PC2_DISPATCH_H(key->Lh, PC2_CALL_DEC)

@@ -13,7 +13,7 @@
 namespace pc2 {
 namespace tc {
 
-// A modulus N of L words (L = 32 or 64) with its two Toeplitz slices (bf16
+// A modulus N of L words (L = 32 or 64) with its two Toeplitz slices (f16
 // bits, K-major, no swizzle: K-block kb of 8 columns is a [rows x 8]
 // row-major slab).
 template <int L>

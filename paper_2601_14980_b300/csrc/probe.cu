@@ -11,10 +11,14 @@
 //   LOHI  mad.lo + mad.hi       a 32x32->64 product from two halves
 // Each step feeds the accumulator back into the multiplier, so no product
 // is loop-invariant (the assembler would otherwise hoist it).
+//   DADD  add.rn.f64 (the FP64 pipe the z/v update of the ADMM uses)
 //   ROW   the carry-chained row of a 64-limb Montgomery product
-//         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc), the exact
-//         instruction pattern of the library's product core; one product per
-//         limb and row.
+//         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc), the
+//         instruction pattern of the integer-pipe engine's product core; one
+//         product per limb and row.
+//   ROWW  the same rows in the wide form of the tensor-core engine's
+//         products: t_j + a_j b + c as one 32x32->64 product and a 64-bit
+//         add, the carry in a register.
 // Cycles come from clock64 around the loop (max over CTAs), time from CUDA
 // events around the launch.
 #include <cuda_runtime.h>
@@ -28,7 +32,7 @@ constexpr int kProbeThreads = 128;
 constexpr int kIlp = 8;
 
 template <int KIND>
-__global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) k_probe(uint32_t seed, int iters, uint32_t* sink,
+__global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW || KIND == PC2_PROBE_ROWW ? 3 : 8) k_probe(uint32_t seed, int iters, uint32_t* sink,
                                                          long long* cycles) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t b = seed * 2654435761u + tid;
@@ -54,6 +58,53 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) 
 #pragma unroll
     for (int j = 0; j < 64; ++j) fold ^= t[j];
     fold ^= c0 ^ c1;
+  } else if constexpr (KIND == PC2_PROBE_ROWW) {
+    uint32_t a[64], t[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      a[j] = b ^ (j * 0x9e3779b9u);
+      t[j] = j;
+    }
+    uint32_t top = 0;
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll 1
+      for (int r = 0; r < 64; ++r) {
+        const uint32_t br = b + r;
+        uint32_t c = 0u;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const uint64_t p = (uint64_t)a[j] * br + t[j] + c;
+          t[j] = (uint32_t)p;
+          c = (uint32_t)(p >> 32);
+        }
+        top ^= c;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 64; ++j) fold ^= t[j];
+    fold ^= top;
+  } else if constexpr (KIND == PC2_PROBE_DADD) {
+    // x <- x + y in IEEE double (the z/v update's arithmetic); y changes the
+    // low bits so nothing is constant
+    double x[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) x[k] = (double)(b + k);
+    const double y = 1.0 + (double)(b & 7u) * 0x1p-40;
+    __syncthreads();
+    t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(x[k]) : "d"(y));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) fold ^= (uint32_t)__double2loint(x[k]);
   } else if constexpr (KIND == PC2_PROBE_WIDE) {
     // x <- lo(x) * b + x: the multiplier input changes every step
     uint64_t x[kIlp];
@@ -113,7 +164,7 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW ? 3 : 8) 
 
 template <int KIND>
 double ops_per_thread(int iters) {
-  if constexpr (KIND == PC2_PROBE_ROW) return (double)iters * 64.0 * 64.0;
+  if constexpr (KIND == PC2_PROBE_ROW || KIND == PC2_PROBE_ROWW) return (double)iters * 64.0 * 64.0;
   else return (double)iters * 16.0 * kIlp;
 }
 
@@ -174,6 +225,8 @@ extern "C" int pc2_probe_mul(int device, int kind, int blocks_per_sm, int iters,
     case PC2_PROBE_WIDE: return run<PC2_PROBE_WIDE>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
     case PC2_PROBE_LOHI: return run<PC2_PROBE_LOHI>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
     case PC2_PROBE_ROW: return run<PC2_PROBE_ROW>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_DADD: return run<PC2_PROBE_DADD>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
+    case PC2_PROBE_ROWW: return run<PC2_PROBE_ROWW>(sms, blocks_per_sm, iters, st, ops, ms, cycles);
     default: return PC2_EINVAL;
   }
 }

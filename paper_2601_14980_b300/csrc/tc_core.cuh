@@ -1,5 +1,5 @@
 // tc_core.cuh -- Montgomery products of 2048-bit operands with the
-// reduction on the tensor cores (tcgen05.mma, bf16 digits, exact FP32
+// reduction on the tensor cores (tcgen05.mma, f16 digits, exact FP32
 // column sums), for the modular exponentiations of libpc2.
 //
 // The part of a modular product that is a dense contraction with an operand
@@ -11,21 +11,23 @@
 // or N.  Over 8-bit digits (x = sum_k x_k 256^k) the column sums
 // C_j = sum_k x_k y_{j-k} are an [elements x digits] matrix times a
 // Toeplitz matrix of the fixed operand's digits.  Digits 0..255 are exact in
-// bf16 and every column sum stays below 256 * 255^2 < 2^24, so the FP32
+// f16 and every column sum stays below 256 * 255^2 < 2^24, so the FP32
 // accumulation of kind::f16 tcgen05.mma is exact.
 //
-// A CTA owns tiles of 128 elements (MMA M = 128, TMEM lane e = element e):
-// warps 0-3 hold one element per thread, warp 4 allocates 4L TMEM columns
-// (L limbs, 4L digits) and serves the MMAs.  Below for L = 64.  One product a <- a b / R mod N:
-//   1. warps 0-3: T = a b by rows on the integer pipe (a in registers, b's
-//      word i read from shared memory before row i); each finished low word
-//      of T is written as four bf16 digits into the A tile;
-//   2. warp 4: m-columns = A x Toeplitz(N'), columns 0..255, into TMEM;
-//   3. warps 0-3: carries over the columns give m, whose digits go into the
-//      A tile;
-//   4. warp 4: columns 256..511 of m N; after they are read, columns
+// A CTA owns tiles of 128 elements (MMA M = 128, TMEM lane e = element e),
+// one element per thread; warp 0 allocates 4L TMEM columns (L limbs, 4L
+// digits) and thread 0 issues the MMAs.  No warp is set aside for the
+// tensor cores: with four warps per CTA a thread may hold 255 registers at
+// two CTAs per SM, enough for a 64-limb operand and its 128-word square.
+// Below for L = 64.  One product a <- a b / R mod N:
+//   1. T = a b by rows on the integer pipe (a in registers, b's word i read
+//      from shared memory before row i); each finished low word of T is
+//      written as four f16 digits into the A tile;
+//   2. thread 0: m-columns = A x Toeplitz(N'), columns 0..255, into TMEM;
+//   3. carries over the columns give m, whose digits go into the A tile;
+//   4. thread 0: columns 256..511 of m N; after they are read, columns
 //      240..255, which fix the carry out of the low half;
-//   5. warps 0-3: U = T_hi + Hi + carry, then U - N when U >= N.
+//   5. U = T_hi + Hi + carry, then U - N when U >= N.
 // For every K-slice s of 16 digits the Toeplitz operand is the same
 // [rows x 16] matrix once the slice's output columns start 16 s further, so
 // a fixed operand costs one small slice (8 KB for N', 8.5 KB for N), and the
@@ -46,7 +48,7 @@ namespace pc2 {
 namespace tc {
 
 constexpr int kTileE = 128;          // elements per tile (MMA M)
-constexpr int kThreads = 160;        // warps 0-3 compute, warp 4 serves the MMAs
+constexpr int kThreads = 128;        // one element per thread; thread 0 also issues the MMAs
 constexpr int kSlab = kTileE * 16;   // bytes of one 8-digit K-block of the A tile
 constexpr long kSpin = 1L << 20;     // bounded waits (a tile's MMAs take microseconds)
 
@@ -75,11 +77,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileE >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B f16 (format fields 0), both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileE >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
@@ -92,9 +94,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Named barrier 1: the compute warps arrive, the serving warp waits.
-__device__ __forceinline__ void bar_arrive1() { asm volatile("bar.arrive 1, %0;" ::"n"(kThreads) : "memory"); }
-__device__ __forceinline__ void bar_sync1() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
 // 16 consecutive TMEM columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -108,13 +107,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 // An exact column sum (an integer below 2^24 held in f32) as an integer.
 __device__ __forceinline__ uint64_t col(uint32_t bits) { return (uint64_t)__float2uint_rz(__uint_as_float(bits)); }
-// The four digits of word w as bf16 (exact: 0..255), two per 32-bit word.
+// The four digits of word w as f16 (exact: 0..255), two per 32-bit word,
+// without conversion instructions: byte b next to the exponent byte 0x64
+// is the f16 number 1024 + b, and one packed subtraction leaves b.
 __device__ __forceinline__ uint2 word_digits(uint32_t w) {
-  const uint32_t f0 = __float_as_uint(__uint2float_rn(w & 0xffu));
-  const uint32_t f1 = __float_as_uint(__uint2float_rn((w >> 8) & 0xffu));
-  const uint32_t f2 = __float_as_uint(__uint2float_rn((w >> 16) & 0xffu));
-  const uint32_t f3 = __float_as_uint(__uint2float_rn(w >> 24));
-  return make_uint2(__byte_perm(f0, f1, 0x7632), __byte_perm(f2, f3, 0x7632));
+  const uint32_t x0 = __byte_perm(w, 0x64646464u, 0x4140), x1 = __byte_perm(w, 0x64646464u, 0x4342);
+  uint32_t d0, d1;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d0) : "r"(x0), "r"(0x64006400u));
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d1) : "r"(x1), "r"(0x64006400u));
+  return make_uint2(d0, d1);
 }
 // Byte offset of word i of element e in the A tile (digits 4i..4i+3 of row e).
 __device__ __forceinline__ uint32_t slot_off(int i, int e) { return (uint32_t)((i >> 1) * kSlab + e * 16 + (i & 1) * 8); }
@@ -125,7 +126,6 @@ struct Smem {
   uint8_t* B1;
   uint8_t* B2;
   uint64_t* bar;
-  volatile uint32_t* cmd;   // 1: another product follows, 0: stop
   uint32_t* tmem_slot;
 };
 // Per-thread state of the compute side.
@@ -139,12 +139,6 @@ struct State {
 struct Prod {
   uint32_t nz, top0, top1;
 };
-
-// Compute warps: tells warp 4 that no product follows (all compute threads call it once).
-__device__ __forceinline__ void stop(const Smem& s) {
-  if (threadIdx.x == 0) *s.cmd = 0u;
-  bar_arrive1();
-}
 
 // The L-limb product (L = 32 or 64): digits, tile and TMEM sizes, and every
 // step that depends on them.
@@ -166,8 +160,7 @@ static __device__ __forceinline__ Smem smem_layout(uint8_t* base) {
   s.B1 = base + kAbytes;
   s.B2 = s.B1 + kB1bytes;
   s.bar = reinterpret_cast<uint64_t*>(s.B2 + kB2bytes);
-  s.cmd = reinterpret_cast<volatile uint32_t*>(s.bar + 1);
-  s.tmem_slot = const_cast<uint32_t*>(s.cmd) + 1;
+  s.tmem_slot = reinterpret_cast<uint32_t*>(s.bar + 1);
   return s;
 }
 
@@ -182,7 +175,7 @@ static __device__ __forceinline__ uint32_t setup(const Smem& s, const Mod<L>& M)
     mbar_init(s.bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if ((threadIdx.x >> 5) == 4) {
+  if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s.tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
@@ -199,49 +192,52 @@ static __device__ __forceinline__ uint32_t setup(const Smem& s, const Mod<L>& M)
 static __device__ __forceinline__ void teardown(uint32_t tmem) {
   fence_before();
   __syncthreads();
-  if ((threadIdx.x >> 5) == 4) {
+  if ((threadIdx.x >> 5) == 0) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
-// Warp 4: issues the three MMA groups of every product until told to stop.
-static __device__ __forceinline__ void serve(const Smem& s, uint32_t tmem) {
-  const bool leader = (threadIdx.x & 31) == 0;
-  const uint32_t a_base = smem_addr(s.A), b1_base = smem_addr(s.B1), b2_base = smem_addr(s.B2);
-  for (;;) {
-    bar_sync1();
-    if (*s.cmd == 0u) break;
+// The three MMA groups of a product (thread 0).
+// m-columns: slice k adds A[:, 16k..16k+15] x B1[0..kD-1-16k] into columns 16k..kD-1.
+static __device__ __forceinline__ void issue_m(const Smem& s, uint32_t tmem) {
+  const uint32_t a_base = smem_addr(s.A), b1_base = smem_addr(s.B1);
+  for (int k = 0; k < kD / 16; ++k)
+    mma_f16(tmem + 16 * k, sdesc(a_base + 2 * k * kSlab, kSlab, 128), sdesc(b1_base, kB1Rows * 16, 128),
+             idesc_f16(kD - 16 * k), k > 0);
+}
+// Columns kD..2kD-1 of m N into TMEM columns 0..kD-1 (the last slice first: it covers them all).
+static __device__ __forceinline__ void issue_hi(const Smem& s, uint32_t tmem) {
+  const uint32_t a_base = smem_addr(s.A), b2_base = smem_addr(s.B2);
+  for (int k = kD / 16 - 1; k >= 0; --k)
+    mma_f16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128), sdesc(b2_base + (kD - 16 * k) * 16, kB2Rows * 16, 128),
+             idesc_f16(16 * k + 16), k != kD / 16 - 1);
+}
+// Columns kD-16..kD-1 of m N into TMEM columns 0..15.
+static __device__ __forceinline__ void issue_carry(const Smem& s, uint32_t tmem) {
+  const uint32_t a_base = smem_addr(s.A), b2_base = smem_addr(s.B2);
+  for (int k = kD / 16 - 1; k >= 0; --k)
+    mma_f16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
+             sdesc(b2_base + (kD - 16 - 16 * k) * 16, kB2Rows * 16, 128), idesc_f16(16), k != kD / 16 - 1);
+}
+// Hands the A tile and TMEM to the tensor cores for one group: every
+// thread's shared-memory writes and TMEM reads are ordered before the
+// barrier, thread 0 issues the group and commits it, and every thread
+// waits (bounded) for its completion.
+template <class Issue>
+static __device__ __forceinline__ void mma_step(const Smem& s, uint32_t tmem, State& st, Issue issue) {
+  async_proxy_fence();
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
     fence_after();
-    // m-columns: slice s adds A[:, 16s..16s+15] x B1[0..kD-1-16s] into columns 16s..kD-1
-    if (leader) {
-      for (int k = 0; k < kD / 16; ++k)
-        mma_bf16(tmem + 16 * k, sdesc(a_base + 2 * k * kSlab, kSlab, 128), sdesc(b1_base, kB1Rows * 16, 128),
-                 idesc_bf16(kD - 16 * k), k > 0);
-      mma_commit(s.bar);
-    }
-    __syncwarp();
-    // columns kD..2kD-1 of m N into TMEM columns 0..kD-1 (the last slice first: it covers them all)
-    bar_sync1();
-    fence_after();
-    if (leader) {
-      for (int k = kD / 16 - 1; k >= 0; --k)
-        mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
-                 sdesc(b2_base + (kD - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16 * k + 16), k != kD / 16 - 1);
-      mma_commit(s.bar);
-    }
-    __syncwarp();
-    // columns kD-16..kD-1 of m N into TMEM columns 0..15
-    bar_sync1();
-    fence_after();
-    if (leader) {
-      for (int k = kD / 16 - 1; k >= 0; --k)
-        mma_bf16(tmem, sdesc(a_base + 2 * k * kSlab, kSlab, 128),
-                 sdesc(b2_base + (kD - 16 - 16 * k) * 16, kB2Rows * 16, 128), idesc_bf16(16), k != kD / 16 - 1);
-      mma_commit(s.bar);
-    }
-    __syncwarp();
+    issue(s, tmem);
+    mma_commit(s.bar);
   }
+  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
+  st.phase ^= 1u;
+  __syncwarp();
+  fence_after();
 }
 
 // Product phase of a general product, element e = threadIdx.x: T = a b with
@@ -252,12 +248,19 @@ static __device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uin
   uint8_t* A = s.A;
 #pragma unroll
   for (int j = 0; j < kL; ++j) t[j] = 0u;
-  uint32_t c0 = 0u, c1 = 0u;
   Prod pr{0u, 0u, 0u};
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < kL; ++i) {
     const uint32_t bi = *reinterpret_cast<const uint32_t*>(A + slot_off(i, e));
-    row_mac<kL>(t, c0, c1, RegA<kL>{a}, bi);
+    // t += a bi: each step a bi_j + t_j + c < 2^64, one wide product and a
+    // 64-bit add, the carry in a register (no carry-flag chain)
+    uint32_t c = 0u;
+#pragma unroll
+    for (int j = 0; j < kL; ++j) {
+      const uint64_t p = (uint64_t)a[j] * bi + t[j] + c;
+      t[j] = (uint32_t)p;
+      c = (uint32_t)(p >> 32);
+    }
     const uint32_t w = t[0];
     pr.nz |= w;
     pr.top0 = i == kL - 2 ? w : pr.top0;
@@ -265,27 +268,26 @@ static __device__ __forceinline__ Prod product_rows(const uint32_t (&a)[kL], uin
     *reinterpret_cast<uint2*>(A + slot_off(i, e)) = word_digits(w);
 #pragma unroll
     for (int j = 0; j < kL - 1; ++j) t[j] = t[j + 1];
-    t[kL - 1] = c0;
-    c0 = c1;
-    c1 = 0u;
+    t[kL - 1] = c;
   }
   return pr;  // T < N^2 < 2^4096: nothing is left above t
 }
 
 // Row i of the squaring's cross products: C += a_i (a_{i+1} .. a_63) at
-// positions 2i+1 .. i+64 (carry into i+65); positions up to 2i+2 are then
-// final, and those below 64 are parked in their slots of the A tile.
+// positions 2i+1 .. i+63 and the row's carry word at i+64 (no earlier row
+// reaches it), one wide product and a 64-bit add per step; positions up to
+// 2i+2 are then final, and those below 64 are parked in their slots of the
+// A tile.
 template <int I>
 static __device__ __forceinline__ void sqr_row(uint32_t (&C)[2 * kL], const uint32_t (&a)[kL], uint8_t* A, int e) {
-  mad_lo_cc(C[2 * I + 1], a[I], a[I + 1]);
+  uint32_t c = 0u;
 #pragma unroll
-  for (int j = I + 2; j < kL; ++j) madc_lo_cc(C[I + j], a[I], a[j]);
-  addc_z(C[I + kL]);
-  mad_hi_cc(C[2 * I + 2], a[I], a[I + 1]);
-#pragma unroll
-  for (int j = I + 2; j < kL; ++j) madc_hi_cc(C[I + j + 1], a[I], a[j]);
-  C[I + kL + 1] = 0u;
-  addc_z(C[I + kL + 1]);
+  for (int j = I + 1; j < kL; ++j) {
+    const uint64_t p = (uint64_t)a[I] * a[j] + C[I + j] + c;
+    C[I + j] = (uint32_t)p;
+    c = (uint32_t)(p >> 32);
+  }
+  C[I + kL] = c;
   if constexpr (2 * I + 1 < kL) *reinterpret_cast<uint32_t*>(A + slot_off(2 * I + 1, e)) = C[2 * I + 1];
   if constexpr (2 * I + 2 < kL) *reinterpret_cast<uint32_t*>(A + slot_off(2 * I + 2, e)) = C[2 * I + 2];
 }
@@ -308,6 +310,7 @@ static __device__ __forceinline__ Prod product_sqr(const uint32_t (&a)[kL], uint
   uint32_t C[2 * kL];
 #pragma unroll
   for (int k = 0; k < kL + 2; ++k) C[k] = 0u;
+  C[2 * kL - 1] = 0u;
   Prod pr{0u, 0u, 0u};
   uint32_t prev = 0u;
   uint64_t carry = 0;
@@ -350,13 +353,7 @@ static __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[k
   const int warp = e >> 5;
   const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
   uint8_t* A = s.A;
-  if (e == 0) *s.cmd = 1u;
-  async_proxy_fence();
-  fence_before();
-  bar_arrive1();
-  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
-  st.phase ^= 1u;
-  fence_after();
+  mma_step(s, tmem, st, [](const Smem& s_, uint32_t t_) { issue_m(s_, t_); });
   // 3. m = (sum_j C_j 256^j) mod R from columns 0..kD-1; its digits into the A tile
   {
     uint64_t carry = 0;
@@ -373,12 +370,7 @@ static __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[k
       }
     }
   }
-  async_proxy_fence();
-  fence_before();
-  bar_arrive1();
-  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
-  st.phase ^= 1u;
-  fence_after();
+  mma_step(s, tmem, st, [](const Smem& s_, uint32_t t_) { issue_hi(s_, t_); });
   // 5a. t += Hi = sum_j C_{kD+j} 256^j
   uint32_t over = 0u;  // bit 32 L of the running sum
   {
@@ -397,11 +389,7 @@ static __device__ __forceinline__ void reduce(uint32_t (&a)[kL], uint32_t (&t)[k
     }
     over = (uint32_t)carry;
   }
-  fence_before();
-  bar_arrive1();
-  st.ok = mbar_wait(s.bar, st.phase) && st.ok;
-  st.phase ^= 1u;
-  fence_after();
+  mma_step(s, tmem, st, [](const Smem& s_, uint32_t t_) { issue_carry(s_, t_); });
   // 5b. carry out of the low half: T_lo + Lo = c R, Lo = sum_{j<kD} C_j 256^j.
   // Lo = F + c' R with F = (R - T_lo) mod R; c' = round((Lo - F) / R) from
   // the top 8 columns and the top 64 bits of F (error below 2^-39).

@@ -29,9 +29,7 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
   extern __shared__ __align__(1024) uint8_t smem[];
   const tc::Smem s = Core::smem_layout(smem);
   const uint32_t tmem = Core::setup(s, P.m);
-  if ((threadIdx.x >> 5) == 4) {
-    Core::serve(s, tmem);
-  } else {
+  {
     tc::State st{0u, true};
     const size_t ntiles = (count + tc::kTileE - 1) / tc::kTileE;
     for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -49,7 +47,6 @@ __global__ void __launch_bounds__(pc2::tc::kThreads, 2)
         for (int j = 0; j < kL; ++j) y[pc2::tiled_index(g, j, kL)] = a[j];
       }
     }
-    tc::stop(s);
     if (!st.ok && status) atomicOr(status, PC2_ST_TIMEOUT);
   }
   Core::teardown(tmem);

@@ -48,9 +48,7 @@ __global__ void __launch_bounds__(tc::kThreads, tc_ctas<L>())
   extern __shared__ __align__(1024) uint8_t smem[];
   const tc::Smem s = Core::smem_layout(smem);
   const uint32_t tmem = Core::setup(s, P.m);
-  if ((threadIdx.x >> 5) == 4) {
-    Core::serve(s, tmem);
-  } else {
+  {
     const int e = threadIdx.x;
     const int ntab = 1 << (P.e.w - 1);
     const size_t ts = tc::kTileE;  // words of one table entry are tc::kTileE apart
@@ -136,7 +134,6 @@ __global__ void __launch_bounds__(tc::kThreads, tc_ctas<L>())
         for (int j = 0; j < L; ++j) xy[tiled_index(g, j, L)] = a[j];
       }
     }
-    tc::stop(s);
     if (!st.ok && status) atomicOr(status, PC2_ST_TIMEOUT);
   }
   Core::teardown(tmem);
@@ -438,11 +435,11 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
 namespace tc {
 namespace {
 
-uint16_t bf16_of_digit(uint32_t d) {
-  const float f = (float)d;
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  return (uint16_t)(u >> 16);  // exact: d < 256 needs 8 significant bits
+// The f16 bits of a digit 0..255 (exact: at most 8 significant bits).
+uint16_t f16_of_digit(uint32_t d) {
+  if (d == 0) return 0;
+  const int e = 31 - __builtin_clz(d);  // d = 2^e (1 + f), f < 1
+  return (uint16_t)(((e + 15) << 10) | ((d << (10 - e)) & 0x3ffu));
 }
 
 // Slice of the Toeplitz matrix of a 4L-digit operand w: row n, K column kk
@@ -453,7 +450,7 @@ void toeplitz_slice(const uint32_t* w, int rows, uint16_t* out) {
     for (int kk = 0; kk < 16; ++kk) {
       const int d = n - kk;
       const uint32_t v = (d >= 0 && d < 4 * L) ? (w[d / 4] >> (8 * (d % 4))) & 0xffu : 0u;
-      out[(kk / 8) * rows * 8 + n * 8 + (kk % 8)] = bf16_of_digit(v);
+      out[(kk / 8) * rows * 8 + n * 8 + (kk % 8)] = f16_of_digit(v);
     }
 }
 

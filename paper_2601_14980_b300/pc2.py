@@ -700,7 +700,7 @@ def hom_matvec(ctx: Context, key: Key, alpha, s, K, n: int, kbits: int = 0, out=
 
 
 # ------------------------------------------------------------------ multiplier probe
-PROBE_LO, PROBE_HI, PROBE_WIDE, PROBE_LOHI, PROBE_ROW = 0, 1, 2, 3, 4
+PROBE_LO, PROBE_HI, PROBE_WIDE, PROBE_LOHI, PROBE_ROW, PROBE_DADD, PROBE_ROWW = 0, 1, 2, 3, 4, 5, 6
 _probe_mul = _sig("pc2_probe_mul", [_i, _i, _i, _i, _vp, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(_i)])
