@@ -37,8 +37,10 @@ UNIT = "Paillier enc+dec ops/s"
 # elements it processes; None once the kernel changes.
 ENC_DRAM_BYTES_PER_ELEM = 114776
 # DRAM bytes (read + write) per element of one k_modexp_tc launch from an ncu
-# capture of the current build; None until one is taken.
-TC_DRAM_BYTES_PER_ELEM = None
+# capture of this build (the power mod p^2 of 2^16 encryptions: 1.590 GB +
+# 0.568 GB), scaled to a launch by the elements it processes; None once the
+# kernel changes.
+TC_DRAM_BYTES_PER_ELEM = 32922
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
 IMAD_PER_CLK_SM = 64   # nominal 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
 CPU_PER_GROUP = 4      # CPU sample: 16 x 4 encryptions, 16-group products, 4 decryptions per step
@@ -908,7 +910,7 @@ def run_gpu(args):
                    "enc_products_per_elem": prod_enc, "dec_products_per_elem": prod_dec,
                    "hom_sum_products_per_elem": prod_sum, "fractions": fr, "engine_ab": engine_ab,
                    "tc_stages_ms": stages,
-                   "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 32768,
+                   "engine": {-1: "automatic (tensor cores from %d elements at 2048 bits)" % 16384,
                               0: "integer pipe", 1: "tensor cores"}[args.engine]},
         "multiplier_probe": probe,
         "roofline": roof,

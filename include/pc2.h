@@ -98,7 +98,7 @@ int pc2_ctx_set_split(pc2_ctx* ctx, int mode);
  * always use the integer pipe.  PC2_EINVAL for another value. */
 #define PC2_ENGINE_IMAD 0
 #define PC2_ENGINE_TC 1
-#define PC2_TC_MIN_COUNT 32768
+#define PC2_TC_MIN_COUNT 16384
 int pc2_ctx_set_engine(pc2_ctx* ctx, int engine);
 /* Stage timing of the tensor-core path (a measurement aid; the paper has no
  * counterpart).  With timing on, each tensor-core encryption or decryption
@@ -481,10 +481,10 @@ int pc2_mont_sqr(pc2_ctx* ctx, const uint32_t* h_n, int limbs, const uint32_t* d
  *   PC2_PROBE_WIDE  mad.wide.u32 (a whole 32x32->64 product, plus a 64-bit add)
  *   PC2_PROBE_LOHI  a 32x32->64 product as mad.lo + mad.hi
  *   PC2_PROBE_DADD  add.rn.f64 (FP64 adds, the pipe of the z/v update)
- *   PC2_PROBE_ROW   the carry-chained rows of a 64-limb Montgomery product,
- *                   the instruction pattern of the integer-pipe engine
+ *   PC2_PROBE_ROW   the rows of a 64-limb Montgomery product as carry-flag
+ *                   chains (mad.lo.cc / madc.hi.cc)
  *   PC2_PROBE_ROWW  the same rows as wide products with 64-bit adds, the
- *                   pattern of the tensor-core engine's integer-pipe half
+ *                   instruction pattern of the library's products
  * Launches blocks_per_sm x SMs CTAs of 128 threads (PC2_EINVAL when that
  * many cannot all be resident, or iters < 1); every thread runs `iters`
  * loop trips of independent accumulators.  Allocates its own small buffers

@@ -8,9 +8,9 @@
 //
 // mont_mul  -- Montgomery product a*b/R mod N by coarsely integrated operand
 //              scanning (CIOS, Koc/Acar/Kaliski 1996): one row t += a*b_i
-//              (two carry chains: low halves, then high halves of the 32x32
-//              products), one row t += m*N with m = t_0 * (-N^-1) mod 2^32,
-//              then a one-word shift.  Each lane keeps the carry word of its
+//              (per word one 32x32->64 product and a 64-bit add, the carry
+//              in a register), one row t += m*N with m = t_0 * (-N^-1) mod
+//              2^32, then a one-word shift; two rows per loop trip.  Each lane keeps the carry word of its
 //              segment separately (a redundant representation); the shift
 //              hands every lane the low word of its upper neighbour by a
 //              warp shuffle, and carries are resolved once, after the last
@@ -105,16 +105,18 @@ struct RegA {
 template <int S, class A>
 __device__ __forceinline__ void row_mac(uint32_t (&t)[S], uint32_t& c0, uint32_t& c1, const A& a, uint32_t b) {
   static_assert(S >= 2, "segments of at least two limbs");
-  mad_lo_cc(t[0], a[0], b);
+  // each step a_j b + t_j + c < 2^64: one wide product and a 64-bit add,
+  // the carry in a register (no carry-flag chain)
+  uint32_t c = 0u;
 #pragma unroll
-  for (int j = 1; j < S; ++j) madc_lo_cc(t[j], a[j], b);
-  addc_cc_z(c0);
-  addc_z(c1);
-  mad_hi_cc(t[1], a[0], b);
-#pragma unroll
-  for (int j = 1; j < S - 1; ++j) madc_hi_cc(t[j + 1], a[j], b);
-  madc_hi_cc(c0, a[S - 1], b);
-  addc_z(c1);
+  for (int j = 0; j < S; ++j) {
+    const uint64_t p = (uint64_t)a[j] * b + t[j] + c;
+    t[j] = (uint32_t)p;
+    c = (uint32_t)(p >> 32);
+  }
+  const uint64_t v = (uint64_t)c0 + c;
+  c0 = (uint32_t)v;
+  c1 += (uint32_t)(v >> 32);
 }
 
 // Final step of mont_mul: t (this lane's words) plus the carry
@@ -186,7 +188,7 @@ __device__ __forceinline__ void mont_mul(uint32_t (&a)[S], const uint32_t* __res
   for (int j = 0; j < S; ++j) t[j] = 0u;
   uint32_t c0 = 0u, c1 = 0u;
   const RegA<S> av{a};
-#pragma unroll 1
+#pragma unroll 2
   for (int i = 0; i < L; ++i) {
     const uint32_t b = bcol[i * bstride];
     row_mac<S>(t, c0, c1, av, b);

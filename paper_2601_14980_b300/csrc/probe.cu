@@ -13,11 +13,10 @@
 // is loop-invariant (the assembler would otherwise hoist it).
 //   DADD  add.rn.f64 (the FP64 pipe the z/v update of the ADMM uses)
 //   ROW   the carry-chained row of a 64-limb Montgomery product
-//         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc), the
-//         instruction pattern of the integer-pipe engine's product core; one
-//         product per limb and row.
-//   ROWW  the same rows in the wide form of the tensor-core engine's
-//         products: t_j + a_j b + c as one 32x32->64 product and a 64-bit
+//         (mad.lo.cc / madc.lo.cc, then mad.hi.cc / madc.hi.cc); one product
+//         per limb and row.
+//   ROWW  the same rows in the wide form of the library's products (both
+//         engines): t_j + a_j b + c as one 32x32->64 product and a 64-bit
 //         add, the carry in a register.
 // Cycles come from clock64 around the loop (max over CTAs), time from CUDA
 // events around the launch.
@@ -27,6 +26,22 @@
 #include "mont.cuh"
 
 namespace {
+
+// t[0..63], (c0, c1) += a * b with carry-flag chains: the low halves of the
+// 32x32 products (mad.lo.cc / madc.lo.cc), then the high halves.
+__device__ __forceinline__ void cc_row(uint32_t (&t)[64], uint32_t& c0, uint32_t& c1, const uint32_t (&a)[64],
+                                       uint32_t b) {
+  pc2::mad_lo_cc(t[0], a[0], b);
+#pragma unroll
+  for (int j = 1; j < 64; ++j) pc2::madc_lo_cc(t[j], a[j], b);
+  pc2::addc_cc_z(c0);
+  pc2::addc_z(c1);
+  pc2::mad_hi_cc(t[1], a[0], b);
+#pragma unroll
+  for (int j = 1; j < 63; ++j) pc2::madc_hi_cc(t[j + 1], a[j], b);
+  pc2::madc_hi_cc(c0, a[63], b);
+  pc2::addc_z(c1);
+}
 
 constexpr int kProbeThreads = 128;
 constexpr int kIlp = 8;
@@ -52,7 +67,7 @@ __global__ void __launch_bounds__(kProbeThreads, KIND == PC2_PROBE_ROW || KIND =
     for (int it = 0; it < iters; ++it) {
 #pragma unroll 1
       for (int r = 0; r < 64; ++r) {
-        pc2::row_mac<64>(t, c0, c1, pc2::RegA<64>{a}, b + r);
+        cc_row(t, c0, c1, a, b + r);
       }
     }
 #pragma unroll

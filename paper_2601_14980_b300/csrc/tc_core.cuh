@@ -298,7 +298,6 @@ static __device__ __forceinline__ void sqr_rows(uint32_t (&C)[2 * kL], const uin
     sqr_rows<I + 1, END>(C, a, A, e);
   }
 }
-
 // Product phase of a squaring, element e = threadIdx.x: T = a^2 = 2 C + D
 // with C = sum_{i<j} a_i a_j 2^(32(i+j)) (rows of shrinking length, fully
 // unrolled, a in registers) and D = sum_i a_i^2 2^(64 i): 2080 word products
