@@ -9,8 +9,9 @@
 // mont_mul  -- Montgomery product a*b/R mod N by coarsely integrated operand
 //              scanning (CIOS, Koc/Acar/Kaliski 1996): one row t += a*b_i
 //              (per word one 32x32->64 product and a 64-bit add, the carry
-//              in a register), one row t += m*N with m = t_0 * (-N^-1) mod
-//              2^32, then a one-word shift; two rows per loop trip.  Each lane keeps the carry word of its
+//              in a register, two rows per loop trip; at 128 limbs two
+//              carry-flag chains, low then high halves), one row t += m*N
+//              with m = t_0 * (-N^-1) mod 2^32, then a one-word shift.  Each lane keeps the carry word of its
 //              segment separately (a redundant representation); the shift
 //              hands every lane the low word of its upper neighbour by a
 //              warp shuffle, and carries are resolved once, after the last
@@ -101,6 +102,32 @@ struct RegA {
   __device__ __forceinline__ uint32_t operator[](int j) const { return v[j]; }
 };
 
+// Row form per operand size, as measured on B300 (every kernel family at
+// its benchmark configuration, both forms bit-identical): wide products win
+// at 32, 64, 96 and 256 limbs (3072-bit encryption 25 % faster, the small
+// LASSO's rounds 14 %), carry-flag chains at 128 limbs (the n^2 powers and
+// products of 2048-bit keys: 22 % faster).
+template <int S, int T>
+constexpr bool wide_rows() {
+  return S * T != 128;
+}
+
+// Carry-flag form: the low halves of the 32x32 products (mad.lo.cc /
+// madc.lo.cc), then the high halves.
+template <int S, class A>
+__device__ __forceinline__ void row_mac_cc(uint32_t (&t)[S], uint32_t& c0, uint32_t& c1, const A& a, uint32_t b) {
+  mad_lo_cc(t[0], a[0], b);
+#pragma unroll
+  for (int j = 1; j < S; ++j) madc_lo_cc(t[j], a[j], b);
+  addc_cc_z(c0);
+  addc_z(c1);
+  mad_hi_cc(t[1], a[0], b);
+#pragma unroll
+  for (int j = 1; j < S - 1; ++j) madc_hi_cc(t[j + 1], a[j], b);
+  madc_hi_cc(c0, a[S - 1], b);
+  addc_z(c1);
+}
+
 // t[0..S-1], (c0, c1) += a[0..S-1] * b   (c0, c1: carry words above the segment)
 template <int S, class A>
 __device__ __forceinline__ void row_mac(uint32_t (&t)[S], uint32_t& c0, uint32_t& c1, const A& a, uint32_t b) {
@@ -188,18 +215,26 @@ __device__ __forceinline__ void mont_mul(uint32_t (&a)[S], const uint32_t* __res
   for (int j = 0; j < S; ++j) t[j] = 0u;
   uint32_t c0 = 0u, c1 = 0u;
   const RegA<S> av{a};
-#pragma unroll 2
-  for (int i = 0; i < L; ++i) {
+  auto step = [&](int i) {
     const uint32_t b = bcol[i * bstride];
-    row_mac<S>(t, c0, c1, av, b);
+    if constexpr (wide_rows<S, T>()) row_mac<S>(t, c0, c1, av, b);
+    else row_mac_cc<S>(t, c0, c1, av, b);
     const uint32_t m = g.bcast(t[0] * np, 0);
-    row_mac<S>(t, c0, c1, n, m);
+    if constexpr (wide_rows<S, T>()) row_mac<S>(t, c0, c1, n, m);
+    else row_mac_cc<S>(t, c0, c1, n, m);
     const uint32_t up = g.from_next(t[0]);
 #pragma unroll
     for (int j = 0; j < S - 1; ++j) t[j] = t[j + 1];
     asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(t[S - 1]) : "r"(up), "r"(c0));
     asm volatile("addc.u32 %0, %1, 0;" : "=r"(c0) : "r"(c1));
     c1 = 0u;
+  };
+  if constexpr (wide_rows<S, T>()) {
+#pragma unroll 2
+    for (int i = 0; i < L; ++i) step(i);
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < L; ++i) step(i);
   }
   mont_finish<S, T>(a, t, c0, c1, n, g);
 }

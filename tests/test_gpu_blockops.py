@@ -126,6 +126,40 @@ def test_zv_update_equals_oracle(env):
     assert np.array_equal(dz.cpu().numpy(), z_ref) and np.array_equal(dv.cpu().numpy(), v_ref)
 
 
+def test_zv_update_edges_all_magnitudes(env):
+    """Eqs. (ty32), (u78) at the threshold's edges and far from them: |v + x|
+    at kappa, just above it, at 1.5 and 2 kappa and next to 2 kappa, far
+    beyond (where z = v + x - kappa rounds back to v + x), subnormal,
+    infinite and NaN sums, both signs, for kappa 0, subnormal, 1, near the
+    largest double, and log-uniform magnitudes over the whole double range;
+    bit-exact against the oracle (NaN as NaN)."""
+    torch, pc2, ctx = env
+    rng = np.random.default_rng(5)
+    tiny = np.nextafter(0.0, 1.0)
+    for kappa in (0.01, 0.0, 1.0, 5 * tiny, 1.2e308, 3.0e-308):
+        k2 = 2 * kappa
+        eps = np.finfo(np.float64).eps
+        pts = [kappa, np.nextafter(kappa, np.inf), 1.5 * kappa, k2, np.nextafter(k2, np.inf), np.nextafter(k2, 0.0),
+               3 * kappa, kappa * 2.0 ** 52, kappa * 2.0 ** 53, kappa * 2.0 ** 60, kappa * (1 + eps), 1e300,
+               np.finfo(np.float64).max, tiny, 2.2250738585072014e-308, 0.0, np.inf, np.nan, 1.0, 1e-300]
+        pts = np.array([p for p in pts if np.isfinite(p) or np.isinf(p) or np.isnan(p)], dtype=np.float64)
+        mags = 10.0 ** rng.uniform(-320, 308, 4000)
+        x = np.concatenate([pts, -pts, mags * rng.choice([-1.0, 1.0], mags.size)])
+        v = np.zeros_like(x)
+        v[len(pts) * 2:] = rng.standard_normal(mags.size) * np.where(rng.random(mags.size) < 0.5, kappa, 1.0)
+        with np.errstate(invalid="ignore", over="ignore"):
+            z_ref = O.soft_threshold(v + x, kappa)
+            v_ref = v + x - z_ref
+        dx, dz, dv = (torch.from_numpy(a.copy()).cuda() for a in (x, np.full(x.size, 7.0), v))
+        pc2.zv_update(ctx, dx, dz, dv, kappa)
+        gz, gv = dz.cpu().numpy(), dv.cpu().numpy()
+        assert np.array_equal(gz.view(np.int64)[~np.isnan(z_ref)], z_ref.view(np.int64)[~np.isnan(z_ref)]), kappa
+        assert np.array_equal(np.isnan(gz), np.isnan(z_ref)), kappa
+        ok = ~np.isnan(v_ref)
+        assert np.array_equal(gv.view(np.int64)[ok], v_ref.view(np.int64)[ok]), kappa
+        assert np.array_equal(np.isnan(gv), np.isnan(v_ref)), kappa
+
+
 def test_quantize_ties_edges_and_flags(env):
     """Eq. (et21) at exact half-way points (round half to even), at the range
     ends and just inside them, for both quantizers, against the oracle; and the
