@@ -34,7 +34,7 @@
 // A tile (64 KB) also holds each element's operand b: word i sits in the
 // first four bytes of the 8-byte slot that T word i overwrites after row i.
 // Shared memory per CTA: 81 KB at L = 64 (two CTAs per SM, 2 x 256 TMEM
-// columns), 41 KB at L = 32 (three CTAs per SM, 3 x 128 columns).
+// columns), 41 KB at L = 32 (four CTAs per SM, 4 x 128 columns).
 #pragma once
 #include <cuda_runtime.h>
 

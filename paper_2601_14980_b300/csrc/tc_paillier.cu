@@ -34,9 +34,9 @@ struct TcExpParams {
 static_assert(sizeof(TcExpParams<64>) + 256 <= 32764, "parameter block too large");
 
 // Resident CTAs per SM of the power kernel: two at 64 limbs (registers and
-// the 64 KB A tile), three at 32 limbs.
+// the 64 KB A tile), four at 32 limbs (4 x 128 TMEM columns, 128 registers).
 template <int L>
-constexpr int tc_ctas() { return L == 64 ? 2 : 3; }
+constexpr int tc_ctas() { return L == 64 ? 2 : 4; }
 
 // x <- x^E (Montgomery domain, L words, tiled, in place).  tabs: per CTA
 // (2^(w-1) + 1) entries of L words x 128 elements (odd powers, then x^2).
@@ -102,11 +102,17 @@ __global__ void __launch_bounds__(tc::kThreads, tc_ctas<L>())
           }
           if (!more) break;
         }
-        if (src < 0) {
-          Core::montsqr(a, s, tmem, P.m.n, st);
-        } else {
-          Core::write_b_global(s, entry(src), ts);
-          Core::montmul(a, s, tmem, P.m.n, st);
+        {
+          // one reduction site for both product forms (a smaller loop body)
+          uint32_t t[L];
+          tc::Prod pr;
+          if (src < 0) {
+            pr = Core::product_sqr(a, t, s);
+          } else {
+            Core::write_b_global(s, entry(src), ts);
+            pr = Core::product_rows(a, t, s);
+          }
+          Core::reduce(a, t, pr, s, tmem, P.m.n, st);
         }
         if (phase == 0) {  // x^2: keep it, restart from x
           uint32_t* t2 = entry(ntab);
