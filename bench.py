@@ -37,10 +37,10 @@ UNIT = "Paillier enc+dec ops/s"
 # elements it processes; None once the kernel changes.
 ENC_DRAM_BYTES_PER_ELEM = 115348
 # DRAM bytes (read + write) per element of one k_modexp_tc launch from an ncu
-# capture of this build (the power mod p^2 of 2^16 encryptions: 1.590 GB +
+# capture of this build (the power mod p^2 of 2^16 encryptions: 1.587 GB +
 # 0.568 GB), scaled to a launch by the elements it processes; None once the
 # kernel changes.
-TC_DRAM_BYTES_PER_ELEM = 32922
+TC_DRAM_BYTES_PER_ELEM = 32886
 WORKLOAD = "paillier_microbench: n=2048-bit, 2^20 plaintexts rint(N(0,1)*2^24)+2^47, encrypt (CRT) -> 16-group ciphertext product -> CRT decrypt of 2^16"
 IMAD_PER_CLK_SM = 64   # nominal 32-bit integer multiply-add lanes per SM per clock (4 SMSPs x 16)
 CPU_PER_GROUP = 4      # CPU sample: 16 x 4 encryptions, 16-group products, 4 decryptions per step
