@@ -273,8 +273,18 @@ int pc2_admm_create(pc2_ctx* ctx, const pc2_key* key, const pc2_admm_params* par
 void pc2_admm_destroy(pc2_admm* admm);
 /* x = z = v = 0, round counter 1 (synchronises `stream`). */
 int pc2_admm_reset(pc2_admm* admm, pc2_stream_t stream);
-/* `rounds` private rounds of Algorithm 1. */
+/* `rounds` private rounds of Algorithm 1.  PC2_EMISSING, before any launch
+ * and with x, z, v and the round counter unchanged, while an edge node is
+ * marked absent (pc2_admm_set_node_present). */
 int pc2_admm_round(pc2_admm* admm, int rounds, pc2_stream_t stream);
+/* Failure detection on the host.  In every round of Algorithm 1 the master
+ * needs each edge node's segment (its x-hat_k; Sec. V reports the waiting
+ * between nodes).  The orchestrator that collects the segments marks node
+ * `node` (0 <= node < K) absent (present = 0) when its segment has not
+ * arrived, and present again when it has; pc2_admm_round refuses to run
+ * while any node is absent.  All nodes start present.  PC2_EINVAL for a bad
+ * node index. */
+int pc2_admm_set_node_present(pc2_admm* admm, int node, int present);
 /* `rounds` plaintext Dis-ADMM rounds (Eq. (sldo091), (ty32), (u78)) on the same state, FP64. */
 int pc2_admm_round_plain(pc2_admm* admm, int rounds, pc2_stream_t stream);
 /* Copies x, z, v (device, N doubles each; any may be NULL) and the next round number (host; synchronises). */

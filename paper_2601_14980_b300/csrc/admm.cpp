@@ -75,6 +75,7 @@ struct pc2_admm {
   std::shared_ptr<void> mvp, modp;  // cached MatvecParams<L2> / ModConst<L2> of n^2
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap = nullptr;
+  std::vector<uint8_t> present;  // per node: its segment of the next round has arrived (1 by default)
   ~pc2_admm() {
     if (graph) cudaGraphExecDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
@@ -421,8 +422,19 @@ void pc2_admm_destroy(pc2_admm* A) {
   delete A;
 }
 
+int pc2_admm_set_node_present(pc2_admm* A, int node, int present) {
+  if (!A || node < 0 || node >= A->K) return PC2_EINVAL;
+  if ((int)A->present.size() != A->K) A->present.assign(A->K, 1);
+  A->present[node] = present ? 1 : 0;
+  return PC2_OK;
+}
+
 int pc2_admm_round(pc2_admm* A, int rounds, pc2_stream_t stream) {
   if (!A || rounds < 0) return PC2_EINVAL;
+  // a round needs every edge node's segment: report a missing one before
+  // any launch, with the state untouched, so the caller can retry
+  for (const uint8_t p : A->present)
+    if (!p) return PC2_EMISSING;
   const cudaStream_t st = (cudaStream_t)stream;
   pc2_ctx* ctx = A->ctx;
   for (int r = 0; r < rounds; ++r) {

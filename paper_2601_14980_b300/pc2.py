@@ -63,6 +63,7 @@ _hom_scal = _sig("pc2_hom_scal", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
 _hom_scal_wide = _sig("pc2_hom_scal_wide", [_vp, _vp, _vp, _vp, _sz, _vp, _vp])
 
 ST_RANGE, ST_QUANT, ST_TIMEOUT = 1, 2, 4
+OK, EINVAL, ERANGE, EKEY, ENOMEM, ECUDA, ETIMEOUT, EMISSING, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 COST_ENCRYPT, COST_ENCRYPT_PUBLIC, COST_DECRYPT = 0, 1, 2  # pc2_key_cost operations
 
 
@@ -320,6 +321,7 @@ _admm_create = _sig("pc2_admm_create", [_vp, _vp, ctypes.POINTER(_AdmmParams), _
 _admm_destroy = _sig("pc2_admm_destroy", [_vp], None)
 _admm_reset = _sig("pc2_admm_reset", [_vp, _vp])
 _admm_round = _sig("pc2_admm_round", [_vp, _i, _vp])
+_admm_set_node_present = _sig("pc2_admm_set_node_present", [_vp, _i, _i])
 _admm_round_plain = _sig("pc2_admm_round_plain", [_vp, _i, _vp])
 _admm_get = _sig("pc2_admm_get", [_vp, _vp, _vp, _vp, ctypes.POINTER(_u32), _vp])
 _admm_set = _sig("pc2_admm_set", [_vp, _vp, _vp, _vp, _u32, _vp])
@@ -373,6 +375,10 @@ class Admm:
 
     def round_plain(self, rounds: int = 1, stream=None):
         _check(_admm_round_plain(self.h, rounds, _stream(stream)), "pc2_admm_round_plain")
+
+    def set_node_present(self, node: int, present: bool):
+        """Marks edge node `node`'s segment as arrived or missing (pc2_admm_set_node_present)."""
+        _check(_admm_set_node_present(self.h, int(node), int(bool(present))), "pc2_admm_set_node_present")
 
     def get(self, stream=None):
         import torch

@@ -74,3 +74,46 @@ def test_shard_bounds():
             assert sum(c for _, c in spans) == total
             assert all(spans[r][0] + spans[r][1] == spans[r + 1][0] for r in range(world - 1))
             assert max(c for _, c in spans) - min(c for _, c in spans) <= 1
+
+
+# ------------------------------------------------------------------ failure detection (host side)
+def _edge(rank, port, drop_round, ready):
+    import torch.distributed as dist
+
+    from paper_2601_14980_b300.dist import post_segment
+
+    store = dist.TCPStore("127.0.0.1", port, 3, False, timeout=__import__("datetime").timedelta(seconds=60))
+    for rnd in (1, 2):
+        if rnd == drop_round:
+            ready.wait(60)  # a delayed node: its segment arrives only after the master gave up waiting
+        post_segment(store, rnd, rank - 1)
+
+
+def test_missing_edge_segment_detected_then_recovered():
+    """Three processes (a master and two edge nodes) share a TCP store on
+    127.0.0.1.  Round 1: both segments arrive.  Round 2: node 1 is late; the
+    master's bounded wait names it as missing; once it arrives, a second
+    wait finds nothing missing."""
+    import datetime
+
+    import torch.distributed as dist
+
+    from paper_2601_14980_b300.dist import missing_segments
+
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    store = dist.TCPStore("127.0.0.1", port, 3, True, timeout=datetime.timedelta(seconds=60), wait_for_workers=False)
+    ready = ctx.Event()
+    procs = [ctx.Process(target=_edge, args=(r, port, 2 if r == 2 else 0, ready)) for r in (1, 2)]
+    for pr in procs:
+        pr.start()
+    try:
+        assert missing_segments(store, 1, [0, 1], timeout_s=30.0) == []
+        assert missing_segments(store, 2, [0, 1], timeout_s=0.5) == [1]
+        ready.set()
+        assert missing_segments(store, 2, [0, 1], timeout_s=30.0) == []
+    finally:
+        ready.set()
+        for pr in procs:
+            pr.join(timeout=60)
+    assert all(pr.exitcode == 0 for pr in procs)

@@ -206,3 +206,33 @@ def test_matvec_forms_bit_identical(env, nbits):
             assert np.array_equal(v.cpu().numpy(), ref.v[t]), (mode, t)
         adm.close()
     assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("per_node", [False, True])
+def test_missing_edge_node_refuses_round_then_resumes(env, per_node):
+    """Failure detection: while an edge node's segment is marked missing the
+    round is refused (PC2_EMISSING) with x, z, v and the round counter
+    untouched; once it is marked present again the rounds continue and match
+    the oracle's iterates bit for bit (batched form, whose rounds replay a
+    CUDA graph, and per-node form)."""
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=1)
+    st, kg, ko, adm = _make(env, L, 1024, per_node=per_node)
+    ref = O.quantized_admm(st, L.lam, L.rho, 3, QP)
+    adm.round(1)
+    x0, z0, v0, r0 = (a.clone() if hasattr(a, "clone") else a for a in adm.get())
+    adm.set_node_present(2, False)
+    with pytest.raises(pc2.Pc2Error) as err:
+        adm.round(1)
+    assert err.value.code == pc2.EMISSING
+    x1, z1, v1, r1 = adm.get()
+    assert r1 == r0 == 2
+    assert torch.equal(x1, x0) and torch.equal(z1, z0) and torch.equal(v1, v0)
+    with pytest.raises(pc2.Pc2Error):
+        adm.set_node_present(L.K, False)      # no such node
+    adm.set_node_present(2, True)
+    adm.round(2)
+    x, z, v, nxt = adm.get()
+    assert nxt == 4
+    assert np.array_equal(x.cpu().numpy(), ref.x[2]) and np.array_equal(v.cpu().numpy(), ref.v[2])
+    assert ctx.status() == 0
