@@ -146,6 +146,29 @@ __global__ void __launch_bounds__(tc::kThreads, tc_ctas<L>())
 }
 
 // ------------------------------------------------------------------ encryption: set-up and finish
+// a = (a + b) mod N for a, b < N (L words; a in registers, b a column).
+template <int L>
+__device__ __forceinline__ void add_mod_reg(uint32_t (&a)[L], const Col& b, const uint32_t* N) {
+  uint64_t c = 0;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    c += (uint64_t)a[j] + b[j];
+    a[j] = (uint32_t)c;
+    c >>= 32;
+  }
+  uint32_t d[L];
+  uint64_t br = 0;
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    const uint64_t t = (uint64_t)a[j] - N[j] - br;
+    d[j] = (uint32_t)t;
+    br = t >> 63;
+  }
+  const bool sub = c != 0 || br == 0;  // the sum is >= N
+#pragma unroll
+  for (int j = 0; j < L; ++j) a[j] = sub ? d[j] : a[j];
+}
+
 // Set-up 1: r R_h mod h for h = p, q (half width) from the raw draw X, the
 // start of the lifted route of LiftConst.
 template <int Lh>
@@ -153,10 +176,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
     k_enc_tc_pre1(const __grid_constant__ EncCrtParams<Lh> P, size_t count, uint32_t* __restrict__ rp,
                   uint32_t* __restrict__ rq, uint32_t* __restrict__ scratch) {
   constexpr int Lp = Lh / 2;
+  extern __shared__ uint32_t pre_sh[];  // word i of this thread's operand at pre_sh[i * kThreads + tid]
   const Layout ly(1);
   const int SW = 2 * Lh + 4;
-  const Col X = ly.slot(scratch, 0 * SW), A = ly.slot(scratch, 1 * SW), B = ly.slot(scratch, 2 * SW),
-            C = ly.slot(scratch, 3 * SW), TT = ly.slot(scratch, 4 * SW);
+  const Col X = ly.slot(scratch, 0 * SW);
+  const Grp<1> g;
+  const Col bsh{pre_sh + threadIdx.x, kThreads};
   for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
     size_t e = base + ly.gl;
     const bool valid = e < count;
@@ -164,16 +189,31 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
     const uint32_t sid = P.round_ptr ? ((*P.round_ptr << 8) | P.kind) : P.stream;
     gen_r(X, P.seed, sid, P.e0 + e, Lh + 2, 2 * Lh);
     for (int h = 0; h < 2; ++h) {
-      const LiftConst<Lh>& H = h ? P.lq : P.lp;
-      // r = x0 + x1 R_h: r R_h = x0 R_h + (x1 R_h) R_h mod h
-      g_to_mont_2l(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, Lp, B, C, TT);  // x1 R_h
-      g_copy_param(B, H.h.r2, Lp);
-      g_mont(A, A, B, H.h.n, H.h.np, Lp, TT);                                  // x1 R_h^2
-      g_mont(C, X, B, H.h.n, H.h.np, Lp, TT);                                  // x0 R_h
-      g_addmod(A, A, C, H.h.n, Lp);                                            // r R_h mod h
+      const ModConst<Lp>& Hm = (h ? P.lq : P.lp).h;
+      // r = x0 + x1 R_h (x0 = words 0..Lp-1, x1 = words Lp..2Lp+1 of the draw):
+      // r R_h = x0 R_h + (x1 R_h) R_h mod h, Montgomery products in registers
+      uint32_t a[Lp];
+#pragma unroll
+      for (int j = 0; j < Lp; ++j) a[j] = X[2 * Lp + j];  // x1's high words
+      mont_mul<Lp, 1>(a, Hm.r3, 1, ParamN{Hm.n}, Hm.np, g);
+#pragma unroll
+      for (int j = 0; j < Lp; ++j) bsh[j] = a[j];
+#pragma unroll
+      for (int j = 0; j < Lp; ++j) a[j] = X[Lp + j];      // x1's low words
+      mont_mul<Lp, 1>(a, Hm.r2, 1, ParamN{Hm.n}, Hm.np, g);
+      add_mod_reg<Lp>(a, bsh, Hm.n);                      // x1 R_h mod h
+      mont_mul<Lp, 1>(a, Hm.r2, 1, ParamN{Hm.n}, Hm.np, g);  // x1 R_h^2
+#pragma unroll
+      for (int j = 0; j < Lp; ++j) bsh[j] = a[j];
+#pragma unroll
+      for (int j = 0; j < Lp; ++j) a[j] = X[j];
+      mont_mul<Lp, 1>(a, Hm.r2, 1, ParamN{Hm.n}, Hm.np, g);  // x0 R_h
+      add_mod_reg<Lp>(a, bsh, Hm.n);                      // r R_h mod h
       uint32_t* out = h ? rq : rp;
-      if (valid)
-        for (int j = 0; j < Lp; ++j) out[tiled_index(e, j, Lp)] = A[j];
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < Lp; ++j) out[tiled_index(e, j, Lp)] = a[j];
+      }
     }
   }
 }
@@ -187,8 +227,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
                   uint32_t* __restrict__ scratch) {
   constexpr int Lp = Lh / 2;
   const Layout ly(1);
-  const int SW = 2 * Lh + 4;
-  const Col A = ly.slot(scratch, 0 * SW), B = ly.slot(scratch, 1 * SW), TT = ly.slot(scratch, 2 * SW);
+  const Grp<1> g;
   for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
     size_t e = base + ly.gl;
     const bool valid = e < count;
@@ -197,47 +236,78 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
       const ModConst<Lh>& M = h ? P.mq : P.mp;
       const LiftConst<Lh>& H = h ? P.lq : P.lp;
       const uint32_t* in = h ? sq1 : sp1;
-      for (int j = 0; j < Lh; ++j) A[j] = j < Lp ? in[tiled_index(e, j, Lp)] : 0u;
-      g_copy_param(B, H.lift, Lh);
-      g_mont(A, A, B, M.n, M.np, Lh, TT);  // s R mod h^2
+      uint32_t a[Lh];
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = j < Lp ? in[tiled_index(e, j, Lp)] : 0u;
+      mont_mul<Lh, 1>(a, H.lift, 1, ParamN{M.n}, M.np, g);  // s R mod h^2
       uint32_t* out = h ? sq : sp;
-      if (valid)
-        for (int j = 0; j < Lh; ++j) out[tiled_index(e, j, Lh)] = A[j];
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < Lh; ++j) out[tiled_index(e, j, Lh)] = a[j];
+      }
     }
   }
 }
 
+// Finish: c = (1 + m n) (r^n mod h^2) mod h^2 per half, then Eq. (gA-C-B).
+// The Montgomery products run in registers (the library's CIOS product, the
+// second operand in a shared-memory column of this thread or in the
+// parameter block); 1 + m n and the recombination's full product use the
+// word-serial glue columns.
 template <int Lh>
 __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
     k_enc_tc_post(const __grid_constant__ EncCrtParams<Lh> P, const uint64_t* __restrict__ m64,
                   const uint32_t* __restrict__ mwide, size_t count, const uint32_t* __restrict__ yp,
                   const uint32_t* __restrict__ yq, uint32_t* __restrict__ out, uint32_t* __restrict__ scratch,
                   int* status, size_t base_out) {
+  extern __shared__ uint32_t post_sh[];  // word i of this thread's operand at post_sh[i * kThreads + tid]
   const Layout ly(1);
   const int SW = 2 * Lh + 4;
   const Col X = ly.slot(scratch, 0 * SW), GM = ly.slot(scratch, 1 * SW), A = ly.slot(scratch, 2 * SW),
-            B = ly.slot(scratch, 3 * SW), C = ly.slot(scratch, 4 * SW), TT = ly.slot(scratch, 5 * SW),
-            CP = ly.slot(scratch, 6 * SW), CQ = ly.slot(scratch, 7 * SW);
+            C = ly.slot(scratch, 4 * SW), CP = ly.slot(scratch, 6 * SW), CQ = ly.slot(scratch, 7 * SW);
+  const Grp<1> g;
+  const Col bsh{post_sh + threadIdx.x, kThreads};
   for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
     size_t e = base + ly.gl;
     const bool valid = e < count;
     if (!valid) e = count - 1;
-    make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid, status);
+    make_gm(GM, A, m64, mwide, e, P.nwords, Lh, 2 * Lh, valid, status);  // 1 + m n, 2 Lh words
     for (int h = 0; h < 2; ++h) {
       const ModConst<Lh>& M = h ? P.mq : P.mp;
       const uint32_t* y = h ? yq : yp;
       const Col& OUT = h ? CQ : CP;
-      for (int j = 0; j < Lh; ++j) A[j] = y[tiled_index(e, j, Lh)];     // (r^n mod h^2) R
-      g_to_mont_2l(B, GM, M.n, M.r2, M.r3, M.np, Lh, C, OUT, TT);      // (1 + m n) R mod h^2
-      g_mont(C, A, B, M.n, M.np, Lh, TT);                               // c_h R
-      g_zero(B, Lh);
-      B[0] = 1u;
-      g_mont(OUT, C, B, M.n, M.np, Lh, TT);                             // c_h
+      uint32_t a[Lh];
+      // (1 + m n) R mod h^2 = mont(lo, R^2) + mont(hi, R^3)
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = GM[Lh + j];
+      mont_mul<Lh, 1>(a, M.r3, 1, ParamN{M.n}, M.np, g);
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) bsh[j] = a[j];
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = GM[j];
+      mont_mul<Lh, 1>(a, M.r2, 1, ParamN{M.n}, M.np, g);
+      add_mod_reg<Lh>(a, bsh, M.n);
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) bsh[j] = a[j];                   // (1 + m n) R mod h^2
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = y[tiled_index(e, j, Lh)];  // (r^n mod h^2) R
+      mont_mul<Lh, 1>(a, bsh.p, bsh.s, ParamN{M.n}, M.np, g);       // c_h R
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) bsh[j] = j == 0 ? 1u : 0u;
+      mont_mul<Lh, 1>(a, bsh.p, bsh.s, ParamN{M.n}, M.np, g);       // c_h
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) OUT[j] = a[j];
     }
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2  (c_p < p^2 < q^2)
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
-    g_copy_param(B, P.pinv2R, Lh);
-    g_mont(C, A, B, P.mq.n, P.mq.np, Lh, TT);
+    {
+      uint32_t a[Lh];
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = A[j];
+      mont_mul<Lh, 1>(a, P.pinv2R, 1, ParamN{P.mq.n}, P.mq.np, g);
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) C[j] = a[j];
+    }
     g_mul(X, C, Lh, PArr{P.p2}, Lh);
     uint64_t c = 0;
     for (int j = 0; j < 2 * Lh; ++j) {
@@ -255,21 +325,32 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, 1))
     k_dec_tc_pre(const __grid_constant__ DecParams<Lh> P, const uint32_t* __restrict__ ct, size_t count,
                  uint32_t* __restrict__ sp, uint32_t* __restrict__ sq, uint32_t* __restrict__ scratch,
                  size_t ebase) {
+  extern __shared__ uint32_t dpre_sh[];  // word i of this thread's operand at dpre_sh[i * kThreads + tid]
   const Layout ly(1);
-  const int SW = 2 * Lh + 4;
-  const Col X = ly.slot(scratch, 0 * SW), A = ly.slot(scratch, 1 * SW), B = ly.slot(scratch, 2 * SW),
-            C = ly.slot(scratch, 3 * SW), TT = ly.slot(scratch, 4 * SW);
+  const Grp<1> g;
+  const Col bsh{dpre_sh + threadIdx.x, kThreads};
   for (size_t base = (size_t)blockIdx.x * ly.G; base < count; base += (size_t)ly.Gtot) {
     size_t e = base + ly.gl;
     const bool valid = e < count;
     if (!valid) e = count - 1;
-    for (int j = 0; j < 2 * Lh; ++j) X[j] = ct[tiled_index(ebase + e, j, 2 * Lh)];
     for (int h = 0; h < 2; ++h) {
       const ModConst<Lh>& M = h ? P.mq : P.mp;
-      g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // c R mod h^2
+      // c R mod h^2 = mont(c_lo, R^2) + mont(c_hi, R^3), products in registers
+      uint32_t a[Lh];
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = ct[tiled_index(ebase + e, Lh + j, 2 * Lh)];
+      mont_mul<Lh, 1>(a, M.r3, 1, ParamN{M.n}, M.np, g);
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) bsh[j] = a[j];
+#pragma unroll
+      for (int j = 0; j < Lh; ++j) a[j] = ct[tiled_index(ebase + e, j, 2 * Lh)];
+      mont_mul<Lh, 1>(a, M.r2, 1, ParamN{M.n}, M.np, g);
+      add_mod_reg<Lh>(a, bsh, M.n);
       uint32_t* s = h ? sq : sp;
-      if (valid)
-        for (int j = 0; j < Lh; ++j) s[tiled_index(e, j, Lh)] = A[j];
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < Lh; ++j) s[tiled_index(e, j, Lh)] = a[j];
+      }
     }
   }
 }
@@ -366,7 +447,9 @@ int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint6
   auto pre1 = k_enc_tc_pre1<Lh>;
   auto pre2 = k_enc_tc_pre2<Lh>;
   auto post = k_enc_tc_post<Lh>;
-  const int g1 = grid_of(pre1, 0, sms), g2 = grid_of(pre2, 0, sms), gpost = grid_of(post, 0, sms);
+  const size_t post_smem = (size_t)Lh * kThreads * 4;  // one operand column per thread
+  const size_t pre1_smem = (size_t)Lp * kThreads * 4;
+  const int g1 = grid_of(pre1, pre1_smem, sms), g2 = grid_of(pre2, 0, sms), gpost = grid_of(post, post_smem, sms);
   if (g1 < 0 || g2 < 0 || gpost < 0) return PC2_ECUDA;
   const size_t sw = 2 * Lh + 4;
   const size_t glue = 8 * sw * (size_t)(g1 > gpost ? (g1 > g2 ? g1 : g2) : (gpost > g2 ? gpost : g2)) * kThreads;
@@ -385,7 +468,7 @@ int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint6
   uint32_t* sq1 = sp1 + vec1;
   uint32_t* ws = sq1 + vec1;
   if (ev) cudaEventRecord(ev[0], st);
-  pre1<<<g1, kThreads, 0, st>>>(P, count, sp1, sq1, ws);
+  pre1<<<g1, kThreads, pre1_smem, st>>>(P, count, sp1, sq1, ws);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
   int rc = launch_power<Lp>(K.p, P.lp.e1, sp1, count, ws, work, status, sms, st);  // s R_h mod p
   if (rc == PC2_OK) rc = launch_power<Lp>(K.q, P.lq.e1, sq1, count, ws, work, status, sms, st);
@@ -398,7 +481,7 @@ int launch_enc_crt_tc(const EncCrtParams<64>& P, const TcKeyMods& K, const uint6
   if (rc == PC2_OK) rc = launch_power<Lh>(K.q2, P.lq.e2, sq, count, ws, work, status, sms, st);
   if (ev) cudaEventRecord(ev[3], st);
   if (rc != PC2_OK) return rc;
-  post<<<gpost, kThreads, 0, st>>>(P, m64, mwide, count, sp, sq, out, ws, status, base);
+  post<<<gpost, kThreads, post_smem, st>>>(P, m64, mwide, count, sp, sq, out, ws, status, base);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? PC2_OK : PC2_ECUDA;
 }
@@ -409,7 +492,8 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
   constexpr int Lh = 64;
   auto pre = k_dec_tc_pre<Lh>;
   auto post = k_dec_tc_post<Lh>;
-  const int gpre = grid_of(pre, 0, sms), gpost = grid_of(post, 0, sms);
+  const size_t dpre_smem = (size_t)Lh * kThreads * 4;  // one operand column per thread
+  const int gpre = grid_of(pre, dpre_smem, sms), gpost = grid_of(post, 0, sms);
   if (gpre < 0 || gpost < 0) return PC2_ECUDA;
   const size_t pre_words = 5 * (size_t)(2 * Lh + 4) * (size_t)gpre * kThreads;
   const size_t post_words = 7 * (size_t)(2 * Lh + 4) * (size_t)gpost * kThreads;
@@ -424,7 +508,7 @@ int launch_dec_crt_tc(const DecParams<64>& P, const TcKeyMods& K, const uint32_t
   uint32_t* sq = scratch + vec;
   uint32_t* ws = scratch + 2 * vec;
   if (ev) cudaEventRecord(ev[0], st);
-  pre<<<gpre, kThreads, 0, st>>>(P, ct, count, sp, sq, ws, base);
+  pre<<<gpre, kThreads, dpre_smem, st>>>(P, ct, count, sp, sq, ws, base);
   if (cudaGetLastError() != cudaSuccess) return PC2_ECUDA;
   if (ev) cudaEventRecord(ev[1], st);
   int rc = launch_power<Lh>(K.p2, P.ep, sp, count, ws, work, status, sms, st);
