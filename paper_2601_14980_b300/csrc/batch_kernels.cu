@@ -18,9 +18,11 @@
 //                   per-operation kernels).
 //
 // The modular exponentiations run on the register Montgomery core (mont.cuh)
-// with the CRT moduli of one-lane classes in constant memory; the few
-// products mod n^2 per element (aggregation, the 28-bit scaling exponent,
-// the product with alpha-hat) run on the word-serial glue.
+// with the CRT moduli of one-lane classes in constant memory; the few other
+// Montgomery products per element (CRT recombination, aggregation, the
+// 28-bit scaling exponent, the product with alpha-hat) run in the lane
+// group's registers where a lane holds at most 32 words, else on the
+// word-serial glue.
 #include <cuda_runtime.h>
 
 #include "admm_dev.cuh"
@@ -56,6 +58,9 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
                                            uint32_t* bsh_all) {
   constexpr int L2 = 2 * Lh, Lp = Lh / 2, G = kThreads / T;
   constexpr int cls = batch_class(Lh);
+  // glue products in registers up to 32 words per lane: the one kernel holds
+  // every key class under one register budget, and wider segments spill
+  constexpr int MS = 32;
   const Grp<T> g;
   const int gl = (int)threadIdx.x / T;
   const BatchKey<Lh>& K = *static_cast<const BatchKey<Lh>*>(P.key[cls]);
@@ -84,14 +89,13 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
     const uint32_t sid = (round << 8) | (which ? 2u : 1u);
     gen_r(X, P.seed, sid, e, Lh + 2, L2);
     gm_u64(GM, A, which ? qv : qz, K.enc.nwords, Lh, L2);
-    enc_half_f<Lh, T>(K.enc.mp, bmod<Lh, 0>(), K.enc.ep, K.enc.lp, bprime<Lh, 0>(), X, GM, CP, A, B, C, TT, tab, bsh,
+    enc_half_f<Lh, T, MS>(K.enc.mp, bmod<Lh, 0>(), K.enc.ep, K.enc.lp, bprime<Lh, 0>(), X, GM, CP, A, B, C, TT, tab, bsh,
                       g);
-    enc_half_f<Lh, T>(K.enc.mq, bmod<Lh, 1>(), K.enc.eq, K.enc.lq, bprime<Lh, 1>(), X, GM, CQ, A, B, C, TT, tab, bsh,
+    enc_half_f<Lh, T, MS>(K.enc.mq, bmod<Lh, 1>(), K.enc.eq, K.enc.lq, bprime<Lh, 1>(), X, GM, CQ, A, B, C, TT, tab, bsh,
                       g);
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
-    g_copy_param(B, K.enc.pinv2R, Lh);
-    g_mont(C, A, B, K.enc.mq.n, K.enc.mq.np, Lh, TT);
+    grp_mont<Lh, T, MS>(C, A, const_col(K.enc.pinv2R), K.enc.mq.n, K.enc.mq.np, TT, g);
     g_mul(X, C, Lh, PArr{K.enc.p2}, Lh);
     const Col OUT = which ? CV : CZ;
     uint64_t c = 0;
@@ -105,29 +109,27 @@ __device__ __forceinline__ void batch_item(const BatchParams& P, const BatchItem
   }
 
   // s-hat R = (z-hat (-v)-hat R^-1) R^3 R^-1 mod n^2
-  g_mont(C, CZ, CV, K.n2.n, K.n2.np, L2, TT);
-  g_copy_param(B, K.n2.r3, L2);
-  g_mont(A, C, B, K.n2.n, K.n2.np, L2, TT);
+  grp_mont<L2, T, MS>(C, CZ, CV, K.n2.n, K.n2.np, TT, g);
+  grp_mont<L2, T, MS>(A, C, const_col(K.n2.r3), K.n2.n, K.n2.np, TT, g);
   // (s-hat^b) R, digits of the widest b of the warp
   const uint64_t bi = P.b[e];
   const uint32_t hi = __reduce_or_sync(PC2_FULL, (uint32_t)(bi >> 32));
   const uint32_t lo = __reduce_or_sync(PC2_FULL, (uint32_t)bi);
   const int bits = hi ? 64 - __clz(hi) : (lo ? 32 - __clz(lo) : 1);
-  g_pow_u64(C, A, bi, kScalWin, (bits + kScalWin - 1) / kScalWin, tab, K.n2.r1, K.n2.n, K.n2.np, L2, TT);
+  grp_pow_u64<L2, T, MS>(C, A, bi, kScalWin, (bits + kScalWin - 1) / kScalWin, tab, K.n2.r1, K.n2.n, K.n2.np, TT, g);
   // x-hat = alpha-hat * s-hat^b mod n^2
   for (int j = 0; j < L2; ++j) B[j] = P.alpha_hat[nd.ct_off + tiled_index(idx, j, L2)];
-  g_mont(X, C, B, K.n2.n, K.n2.np, L2, TT);
+  grp_mont<L2, T, MS>(X, C, B, K.n2.n, K.n2.np, TT, g);
   if (write) write_tiled<T>(P.xhat + nd.ct_off, idx, X, L2, g);
   __syncwarp();
 
   // D = decrypt(x-hat): CRT halves, Garner m = m_p + p [(m_q - m_p) p^-1 mod q]
-  dec_half_f<Lh, T>(K.dec.mp, bmod<Lh, 0>(), K.dec.ep, K.dec.p, K.dec.pnp, K.dec.pinvlo, K.dec.hpR, X, CP, A, B, C, TT, tab, bsh,
+  dec_half_f<Lh, T, MS>(K.dec.mp, bmod<Lh, 0>(), K.dec.ep, K.dec.p, K.dec.pnp, K.dec.pinvlo, K.dec.hpR, X, CP, A, B, C, TT, tab, bsh,
                        g);
-  dec_half_f<Lh, T>(K.dec.mq, bmod<Lh, 1>(), K.dec.eq, K.dec.q, K.dec.qnp, K.dec.qinvlo, K.dec.hqR, X, CQ, A, B, C, TT, tab, bsh,
+  dec_half_f<Lh, T, MS>(K.dec.mq, bmod<Lh, 1>(), K.dec.eq, K.dec.q, K.dec.qnp, K.dec.qinvlo, K.dec.hqR, X, CQ, A, B, C, TT, tab, bsh,
                        g);
   if (g_sub(A, CQ, CP, Lp)) g_add(A, A, PArr{K.dec.q}, Lp);
-  g_copy_param(B, K.dec.pinvqR, Lp);
-  g_mont(C, A, B, K.dec.q, K.dec.qnp, Lp, TT);
+  grp_mont<Lp, T, MS>(C, A, const_col(K.dec.pinvqR), K.dec.q, K.dec.qnp, TT, g);
   g_mul(X, C, Lp, PArr{K.dec.p}, Lp);
   {
     uint64_t c = 0;

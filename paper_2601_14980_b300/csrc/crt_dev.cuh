@@ -30,7 +30,7 @@ __device__ __forceinline__ void gm_u64(const Col& GM, const Col& M, uint64_t m, 
 // T > 1 each lane loads its segment of Mg.n, Hg.h.n into registers instead).
 // r^n mod h^2 takes the lifted route (LiftConst) where a lane holds at least
 // two half-width limbs, else the power by n mod h(h-1) (schedule E).
-template <int Lh, int T>
+template <int Lh, int T, int MaxS = 64>
 __device__ __forceinline__ void enc_half_f(const ModConst<Lh>& Mg, const uint32_t* nfast, const Sched<kMaxSched>& E,
                                            const LiftConst<Lh>& Hg, const uint32_t* hfast, const Col& X,
                                            const Col& GM, const Col& OUT, const Col& A, const Col& B, const Col& C,
@@ -40,7 +40,7 @@ __device__ __forceinline__ void enc_half_f(const ModConst<Lh>& Mg, const uint32_
   if constexpr (lift_route<Lh, T>()) {
     rn_lifted<Lh, T>(Mg, nfast, Hg, hfast, X, A, B, C, TT, tab, bsh, g);  // (r^n mod h^2) R
   } else {
-    g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // r R mod h^2
+    grp_to_mont_2l<Lh, T, MaxS>(A, X, Mg.n, Mg.r2, Mg.r3, np, B, C, TT, g);  // r R mod h^2
     __syncwarp();
     uint32_t a[S];
     load_seg(a, A, g);
@@ -49,15 +49,15 @@ __device__ __forceinline__ void enc_half_f(const ModConst<Lh>& Mg, const uint32_
     store_seg(A, a, g);
     __syncwarp();
   }
-  g_to_mont_2l(B, GM, Mg.n, Mg.r2, Mg.r3, np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
-  g_mont(C, A, B, Mg.n, np, Lh, TT);
+  grp_to_mont_2l<Lh, T, MaxS>(B, GM, Mg.n, Mg.r2, Mg.r3, np, C, OUT, TT, g);  // (1 + m n) R mod h^2
+  grp_mont<Lh, T, MaxS>(C, A, B, Mg.n, np, TT, g);
   g_zero(B, Lh);
   B[0] = 1u;
-  g_mont(OUT, C, B, Mg.n, np, Lh, TT);
+  grp_mont<Lh, T, MaxS>(OUT, C, B, Mg.n, np, TT, g);
 }
 
 // One CRT half of a decryption: OUT = L_h(c^(h-1) mod h^2) h_h mod h.
-template <int Lh, int T>
+template <int Lh, int T, int MaxS = 64>
 __device__ __forceinline__ void dec_half_f(const ModConst<Lh>& Mg, const uint32_t* nfast,
                                            const Sched<kMaxSchedHalf>& E, const uint32_t* h,
                                            uint32_t hnp, const uint32_t* hinvlo, const uint32_t* hhR, const Col& X,
@@ -65,7 +65,7 @@ __device__ __forceinline__ void dec_half_f(const ModConst<Lh>& Mg, const uint32_
                                            const Col& tab, const Col& bsh, const Grp<T>& g) {
   constexpr int S = Lh / T, Lp = Lh / 2;
   const uint32_t np = Mg.np;
-  g_to_mont_2l(A, X, Mg.n, Mg.r2, Mg.r3, np, Lh, B, C, TT);  // c R mod h^2
+  grp_to_mont_2l<Lh, T, MaxS>(A, X, Mg.n, Mg.r2, Mg.r3, np, B, C, TT, g);  // c R mod h^2
   __syncwarp();
   uint32_t a[S];
   load_seg(a, A, g);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void dec_half_f(const ModConst<Lh>& Mg, const uint32_
   __syncwarp();
   g_zero(B, Lh);
   B[0] = 1u;
-  g_mont(C, A, B, Mg.n, np, Lh, TT);  // x = c^(h-1) mod h^2 = 1 mod h
+  grp_mont<Lh, T, MaxS>(C, A, B, Mg.n, np, TT, g);  // x = c^(h-1) mod h^2 = 1 mod h
   {
     uint64_t br = 1;
     for (int j = 0; j < Lh && br; ++j) {
@@ -85,25 +85,26 @@ __device__ __forceinline__ void dec_half_f(const ModConst<Lh>& Mg, const uint32_
     }
   }
   g_mul_lo(A, C, PArr{hinvlo}, Lp);  // (x - 1) / h exactly
-  g_copy_param(B, hhR, Lp);
-  g_mont(OUT, A, B, h, hnp, Lp, TT);
+  grp_mont<Lp, T, MaxS>(OUT, A, const_col(hhR), h, hnp, TT, g);
 }
 
 // acc = base^k in Montgomery form (base given as x R), fixed windows of w
-// bits over nd digits (warp-uniform); tab: 2^w entries of len words.
-__device__ __forceinline__ void g_pow_u64(const Col& acc, const Col& base, uint64_t k, int w, int nd, const Col& tab,
-                                          const uint32_t* r1, const uint32_t* N, uint32_t np, int len,
-                                          const Col& tt) {
+// bits over nd digits (warp-uniform); tab: 2^w entries of L words.  The
+// products go through the lane group (grp_mont).
+template <int L, int T, int MaxS = 64>
+__device__ __forceinline__ void grp_pow_u64(const Col& acc, const Col& base, uint64_t k, int w, int nd, const Col& tab,
+                                            const uint32_t* r1, const uint32_t* N, uint32_t np, const Col& tt,
+                                            const Grp<T>& g) {
   const int ntab = 1 << w;
   const uint64_t mask = (uint64_t)ntab - 1u;
-  g_copy_param(tab, r1, len);
-  g_copy(tab.off(len), base, len);
-  for (int d = 2; d < ntab; ++d) g_mont(tab.off(d * len), tab.off((d - 1) * len), tab.off(len), N, np, len, tt);
+  g_copy_param(tab, r1, L);
+  g_copy(tab.off(L), base, L);
+  for (int d = 2; d < ntab; ++d) grp_mont<L, T, MaxS>(tab.off(d * L), tab.off((d - 1) * L), tab.off(L), N, np, tt, g);
   int pos = nd - 1;
-  g_copy(acc, tab.off((int)((k >> (pos * w)) & mask) * len), len);
+  g_copy(acc, tab.off((int)((k >> (pos * w)) & mask) * L), L);
   for (--pos; pos >= 0; --pos) {
-    for (int s = 0; s < w; ++s) g_mont(acc, acc, acc, N, np, len, tt);
-    g_mont(acc, acc, tab.off((int)((k >> (pos * w)) & mask) * len), N, np, len, tt);
+    for (int s = 0; s < w; ++s) grp_mont<L, T, MaxS>(acc, acc, acc, N, np, tt, g);
+    grp_mont<L, T, MaxS>(acc, acc, tab.off((int)((k >> (pos * w)) & mask) * L), N, np, tt, g);
   }
 }
 

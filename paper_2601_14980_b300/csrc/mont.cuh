@@ -482,6 +482,49 @@ __device__ __forceinline__ void g_to_mont_2l(const Col d, const Col x, const uin
   g_mont(t2, x.off(len), t2, N, np, len, tt);   // x_hi * R^2 = x_hi * 2^(32 len) * R
   g_addmod(d, t1, t2, N, len);
 }
+// ---------------------------------------------------------------- glue products by the lane group
+// The glue runs the same word-serial code on every lane of an element's
+// group; its Montgomery products instead go through mont_mul: lane k holds
+// words k S .. k S + S - 1 of a (S = L / T) in registers, b is read word by
+// word from its column (global scratch, shared memory or a constant array,
+// stride b.s), N from the pointer (T = 1) or as register segments (T > 1).
+// The result is the same canonical integer as g_mont's.  d may alias a or b
+// (every lane has read both before any lane writes d).  With fewer than two
+// words per lane, or more than MaxS (the segment and its carries would not
+// fit the kernel's register budget), it falls back to g_mont.
+template <int L, int T, int MaxS = 64>
+__device__ __forceinline__ void grp_mont(const Col& d, const Col& a, const Col& b, const uint32_t* N, uint32_t np,
+                                         const Col& tt, const Grp<T>& g) {
+  constexpr int S = L / T;
+  if constexpr (S < 2 || S > MaxS) {
+    g_mont(d, a, b, N, np, L, tt);
+  } else {
+    if constexpr (T > 1) __syncwarp();
+    uint32_t x[S];
+    load_seg(x, a, g);
+    if constexpr (T == 1) {
+      mont_mul<S, 1>(x, b.p, b.s, ParamN{N}, np, g);
+    } else {
+      const RegN<S> rn = reg_n<S, T>(N, g);
+      mont_mul<S, T>(x, b.p, b.s, rn, np, g);
+      __syncwarp();
+    }
+    store_seg(d, x, g);
+    if constexpr (T > 1) __syncwarp();
+  }
+}
+// A constant array (parameter block or device memory) as a column.
+__device__ __forceinline__ Col const_col(const uint32_t* v) { return Col{const_cast<uint32_t*>(v), 1}; }
+// g_to_mont_2l with the two products by the lane group.
+template <int L, int T, int MaxS = 64>
+__device__ __forceinline__ void grp_to_mont_2l(const Col& d, const Col& x, const uint32_t* N, const uint32_t* r2,
+                                               const uint32_t* r3, uint32_t np, const Col& t1, const Col& t2,
+                                               const Col& tt, const Grp<T>& g) {
+  grp_mont<L, T, MaxS>(t1, x, const_col(r2), N, np, tt, g);         // x_lo * R
+  grp_mont<L, T, MaxS>(t2, x.off(L), const_col(r3), N, np, tt, g);  // x_hi * R^2
+  g_addmod(d, t1, t2, N, L);
+}
+
 // d[0..la+lb) = a[0..la) * b[0..lb) (schoolbook)
 template <class B>
 __device__ __forceinline__ void g_mul(const Col& d, const Col& a, int la, const B& b, int lb) {

@@ -113,11 +113,10 @@ __device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const uint32_t*
   constexpr int Lp = Lh / 2, Sa = Lp / T, S = Lh / T;
   // r = x0 + x1 R_h with x0 = words [0, Lp), x1 = words [Lp, 3 Lp) < R_h^2:
   // r R_h = x0 R_h + (x1 R_h) R_h mod h
-  g_to_mont_2l(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, Lp, B, C, TT);  // x1 R_h
-  g_copy_param(B, H.h.r2, Lp);
-  g_mont(A, A, B, H.h.n, H.h.np, Lp, TT);                                  // x1 R_h^2
-  g_mont(C, X, B, H.h.n, H.h.np, Lp, TT);                                  // x0 R_h
-  g_addmod(A, A, C, H.h.n, Lp);                                            // r R_h mod h
+  grp_to_mont_2l<Lp, T>(A, X.off(Lp), H.h.n, H.h.r2, H.h.r3, H.h.np, B, C, TT, g);  // x1 R_h
+  grp_mont<Lp, T>(A, A, const_col(H.h.r2), H.h.n, H.h.np, TT, g);                  // x1 R_h^2
+  grp_mont<Lp, T>(C, X, const_col(H.h.r2), H.h.n, H.h.np, TT, g);                  // x0 R_h
+  g_addmod(A, A, C, H.h.n, Lp);                                                    // r R_h mod h
   __syncwarp();
   {
     uint32_t a[Sa];
@@ -127,8 +126,7 @@ __device__ __forceinline__ void rn_lifted(const ModConst<Lh>& M, const uint32_t*
   }
   __syncwarp();
   for (int j = Lp; j < Lh; ++j) A[j] = 0u;
-  g_copy_param(B, H.lift, Lh);
-  g_mont(A, A, B, M.n, M.np, Lh, TT);                                      // s R mod h^2
+  grp_mont<Lh, T>(A, A, const_col(H.lift), M.n, M.np, TT, g);             // s R mod h^2
   __syncwarp();
   uint32_t a[S];
   load_seg(a, A, g);
@@ -147,7 +145,7 @@ __device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMax
     rn_lifted<Lh, T>(M, M.n, H, H.h.n, X, A, B, C, TT, tab, bsh, g);
   } else {
     // direct route: the power by n mod h(h-1)
-    g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // r~ = r R mod h^2
+    grp_to_mont_2l<Lh, T>(A, X, M.n, M.r2, M.r3, M.np, B, C, TT, g);  // r~ = r R mod h^2
     __syncwarp();
     uint32_t a[S];
     load_seg(a, A, g);
@@ -155,11 +153,11 @@ __device__ __forceinline__ void enc_half(const ModConst<Lh>& M, const Sched<kMax
     store_seg(A, a, g);
     __syncwarp();
   }
-  g_to_mont_2l(B, GM, M.n, M.r2, M.r3, M.np, Lh, C, OUT, TT);  // (1 + m n) R mod h^2
-  g_mont(C, A, B, M.n, M.np, Lh, TT);                          // c_h R
+  grp_to_mont_2l<Lh, T>(B, GM, M.n, M.r2, M.r3, M.np, C, OUT, TT, g);  // (1 + m n) R mod h^2
+  grp_mont<Lh, T>(C, A, B, M.n, M.np, TT, g);                          // c_h R
   g_zero(B, Lh);
   B[0] = 1u;
-  g_mont(OUT, C, B, M.n, M.np, Lh, TT);                        // c_h
+  grp_mont<Lh, T>(OUT, C, B, M.n, M.np, TT, g);                        // c_h
 }
 
 template <int Lh, int T>
@@ -189,8 +187,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt(const _
     enc_half<Lh, T>(P.mq, P.eq, P.lq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
     // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2  (c_p < p^2 < q^2)
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
-    g_copy_param(B, P.pinv2R, Lh);
-    g_mont(C, A, B, P.mq.n, P.mq.np, Lh, TT);
+    grp_mont<Lh, T>(C, A, const_col(P.pinv2R), P.mq.n, P.mq.np, TT, g);
     g_mul(X, C, Lh, PArr{P.p2}, Lh);
     uint64_t c = 0;
     for (int j = 0; j < 2 * Lh; ++j) {
@@ -242,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(L2, T)) k_enc_pub(const _
     store_seg(A, a, g);
     __syncwarp();
     make_gm(GM, X, m64, mwide, e, P.nwords, Ln, L2, valid, status);
-    g_mont(X, A, GM, P.m.n, P.m.np, L2, TT);  // r^n (1 + m n) mod n^2
+    grp_mont<L2, T>(X, A, GM, P.m.n, P.m.np, TT, g);  // r^n (1 + m n) mod n^2
     if (valid) write_tiled<T>(out, e, X, L2, g);
     __syncwarp();
   }
@@ -255,7 +252,7 @@ __device__ __forceinline__ void dec_half(const ModConst<Lh>& M, const Sched<kMax
                                          const Col& OUT, const Col& A, const Col& B, const Col& C, const Col& TT,
                                          const Col& tab, const Col& bsh, const Grp<T>& g) {
   constexpr int S = Lh / T, Lp = Lh / 2;
-  g_to_mont_2l(A, X, M.n, M.r2, M.r3, M.np, Lh, B, C, TT);  // c R mod h^2
+  grp_to_mont_2l<Lh, T>(A, X, M.n, M.r2, M.r3, M.np, B, C, TT, g);  // c R mod h^2
   __syncwarp();
   uint32_t a[S];
   load_seg(a, A, g);
@@ -264,7 +261,7 @@ __device__ __forceinline__ void dec_half(const ModConst<Lh>& M, const Sched<kMax
   __syncwarp();
   g_zero(B, Lh);
   B[0] = 1u;
-  g_mont(C, A, B, M.n, M.np, Lh, TT);  // x = c^(h-1) mod h^2, x = 1 mod h
+  grp_mont<Lh, T>(C, A, B, M.n, M.np, TT, g);  // x = c^(h-1) mod h^2, x = 1 mod h
   // x - 1 (x >= 1)
   {
     uint64_t br = 1;
@@ -275,8 +272,7 @@ __device__ __forceinline__ void dec_half(const ModConst<Lh>& M, const Sched<kMax
     }
   }
   g_mul_lo(A, C, PArr{hinvlo}, Lp);   // L_h(x) = (x-1)/h exactly, via h^-1 mod 2^(32 Lp)
-  g_copy_param(B, hhR, Lp);
-  g_mont(OUT, A, B, h, hnp, Lp, TT);  // m_h = L_h(x) h_h mod h
+  grp_mont<Lp, T>(OUT, A, const_col(hhR), h, hnp, TT, g);  // m_h = L_h(x) h_h mod h
 }
 
 template <int Lh, int T>
@@ -304,8 +300,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt(const _
     dec_half<Lh, T>(P.mq, P.eq, P.q, P.qnp, P.qinvlo, P.hqR, X, MQ, A, B, C, TT, tab, bsh, g);
     // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q]  (m_p < p < q)
     if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{P.q}, Lp);
-    g_copy_param(B, P.pinvqR, Lp);
-    g_mont(C, A, B, P.q, P.qnp, Lp, TT);
+    grp_mont<Lp, T>(C, A, const_col(P.pinvqR), P.q, P.qnp, TT, g);
     g_mul(X, C, Lp, PArr{P.p}, Lp);
     uint64_t c = 0;
     for (int j = 0; j < Lh; ++j) {
@@ -365,8 +360,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_enc_crt2(const 
       // Eq. (gA-C-B) with c_q from the partner group (gl + H) of this CTA
       const Col CP = CH, CQ{CH.p + H, CH.s};
       if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{P.mq.n}, Lh);
-      g_copy_param(B, P.pinv2R, Lh);
-      g_mont(C, A, B, P.mq.n, P.mq.np, Lh, TT);
+      grp_mont<Lh, T>(C, A, const_col(P.pinv2R), P.mq.n, P.mq.np, TT, g);
       g_mul(X, C, Lh, PArr{P.p2}, Lh);
       uint64_t c = 0;
       for (int j = 0; j < 2 * Lh; ++j) {
@@ -410,8 +404,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(Lh, T)) k_dec_crt2(const 
       // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q], m_q from the partner group
       const Col MP = MH, MQ{MH.p + H, MH.s};
       if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{P.q}, Lp);
-      g_copy_param(B, P.pinvqR, Lp);
-      g_mont(C, A, B, P.q, P.qnp, Lp, TT);
+      grp_mont<Lp, T>(C, A, const_col(P.pinvqR), P.q, P.qnp, TT, g);
       g_mul(X, C, Lp, PArr{P.p}, Lp);
       uint64_t c = 0;
       for (int j = 0; j < Lh; ++j) {

@@ -53,8 +53,7 @@ __device__ __forceinline__ void serve_encrypt(const ServeKey<Lh>& K, const Serve
   enc_half_f<Lh, T>(K.enc.mq, serve_const<Lh>().mq, K.enc.eq, K.enc.lq, serve_const<Lh>().hq, X, GM, CQ, A, B, C, TT, tab, bsh, g);
   // Eq. (gA-C-B): c = c_p + [(c_q - c_p) (p^2)^-1 mod q^2] p^2
   if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
-  g_copy_param(B, K.enc.pinv2R, Lh);
-  g_mont(C, A, B, K.enc.mq.n, K.enc.mq.np, Lh, TT);
+  grp_mont<Lh, T>(C, A, const_col(K.enc.pinv2R), K.enc.mq.n, K.enc.mq.np, TT, g);
   g_mul(X, C, Lh, PArr{K.enc.p2}, Lh);
   uint64_t c = 0;
   for (int j = 0; j < L2; ++j) {
@@ -87,8 +86,7 @@ __device__ __forceinline__ void serve_decrypt(const ServeKey<Lh>& K, const Serve
                     B, C, TT, tab, bsh, g);
   // Garner: m = m_p + p [(m_q - m_p) p^-1 mod q]
   if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{K.dec.q}, Lp);
-  g_copy_param(B, K.dec.pinvqR, Lp);
-  g_mont(C, A, B, K.dec.q, K.dec.qnp, Lp, TT);
+  grp_mont<Lp, T>(C, A, const_col(K.dec.pinvqR), K.dec.q, K.dec.qnp, TT, g);
   g_mul(X, C, Lp, PArr{K.dec.p}, Lp);
   uint64_t c = 0;
   for (int j = 0; j < Lh; ++j) {
@@ -125,8 +123,7 @@ __device__ __forceinline__ void serve_encrypt_split(const ServeKey<Lh>& K, const
   if (!half) {
     const Col CP = CH, CQ{CH.p + H, CH.s};
     if (g_sub(A, CQ, CP, Lh)) g_add(A, A, PArr{K.enc.mq.n}, Lh);
-    g_copy_param(B, K.enc.pinv2R, Lh);
-    g_mont(C, A, B, K.enc.mq.n, K.enc.mq.np, Lh, TT);
+    grp_mont<Lh, T>(C, A, const_col(K.enc.pinv2R), K.enc.mq.n, K.enc.mq.np, TT, g);
     g_mul(X, C, Lh, PArr{K.enc.p2}, Lh);
     uint64_t c = 0;
     for (int j = 0; j < L2; ++j) {
@@ -163,8 +160,7 @@ __device__ __forceinline__ void serve_decrypt_split(const ServeKey<Lh>& K, const
   if (!half) {
     const Col MP = MH, MQ{MH.p + H, MH.s};
     if (g_sub(A, MQ, MP, Lp)) g_add(A, A, PArr{K.dec.q}, Lp);
-    g_copy_param(B, K.dec.pinvqR, Lp);
-    g_mont(C, A, B, K.dec.q, K.dec.qnp, Lp, TT);
+    grp_mont<Lp, T>(C, A, const_col(K.dec.pinvqR), K.dec.q, K.dec.qnp, TT, g);
     g_mul(X, C, Lp, PArr{K.dec.p}, Lp);
     uint64_t c = 0;
     for (int j = 0; j < Lh; ++j) {
