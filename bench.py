@@ -33,9 +33,9 @@ SEED, STREAM = 0xB300, 1
 METRIC = "Paillier enc/dec per s @2048-bit"
 UNIT = "Paillier enc+dec ops/s"
 # DRAM bytes (read + write) per element of k_enc_crt<64,1> from one ncu capture
-# of this build (2^17 elements: 10.87 GB + 4.25 GB), scaled to a launch by the
+# of this build (2^17 elements: 10.72 GB + 3.97 GB), scaled to a launch by the
 # elements it processes; None once the kernel changes.
-ENC_DRAM_BYTES_PER_ELEM = 115348
+ENC_DRAM_BYTES_PER_ELEM = 112059
 # DRAM bytes (read + write) per element of one k_modexp_tc launch from an ncu
 # capture of this build (the power mod p^2 of 2^16 encryptions: 1.587 GB +
 # 0.568 GB), scaled to a launch by the elements it processes; None once the
