@@ -326,6 +326,10 @@ int pc2_admm_info(const pc2_admm* admm, int* c, int* nwin, int* ntiles);
  * of element tiles ordered longest first, captured once as a CUDA graph and
  * replayed (a device round counter advances the r-streams); it uses constant
  * memory of the library, so one batched round at a time may run per device.
+ * Nodes of a 2048-bit key that the tensor-core engine takes (PC2_TC_MIN_COUNT
+ * elements or more with the engine automatic, any size with it forced to
+ * PC2_ENGINE_TC; decided at pc2_batch_create) stay out of the work list: each
+ * batched round runs them node by node, as below, before the launch.
  * pc2_batch_round_per_node runs the same round node by node through the
  * per-operation kernels (pc2_encrypt, pc2_hom_add, pc2_hom_scal,
  * pc2_decrypt) and gives bit-identical state.  Status bits: PC2_ST_QUANT
@@ -360,7 +364,8 @@ int pc2_batch_get(pc2_batch* batch, double* d_x, double* d_z, double* d_v, uint3
 /* Device pointer of node `node`'s tiled ciphertexts of the last round
  * (which: 0 alpha-hat, 1 z-hat, 2 (-v)-hat, 3 x-hat) and their limbs (2 L(n)). */
 int pc2_batch_ciphertexts(pc2_batch* batch, int which, int node, const uint32_t** d_tiled, int* limbs);
-/* Elements, work items, persistent grid and scratch bytes of the batched launch. */
+/* Elements, work items, persistent grid and scratch bytes of the batched
+ * launch (the work items leave out the tensor-core nodes). */
 int pc2_batch_info(const pc2_batch* batch, size_t* elements, int* items, int* grid, size_t* scratch_bytes);
 /* Autotuner: times the window width (4..6) of each key's exponent schedules
  * and the CTAs per SM (1..3) of the persistent launch on a sample of the work

@@ -5,7 +5,12 @@
 //
 // Work items hold up to 128 / lanes consecutive elements of one node; they
 // are ordered by their expected duration (longest first) so the persistent
-// CTAs finish together.  The autotuner (pc2_batch_tune) times the window
+// CTAs finish together.  Nodes of 2048-bit keys large enough for the
+// tensor-core engine (PC2_TC_MIN_COUNT elements or more, engine automatic,
+// or the engine forced to the tensor cores) hold no work items: a batched
+// round runs them node by node through the per-operation entry points
+// first, then the persistent launch over the other nodes, which advances
+// the round counter for both.  The autotuner (pc2_batch_tune) times the window
 // widths of each key's exponent schedules and the CTAs per SM on a sample
 // of the work list without touching the state.
 #include <cuda_runtime.h>
@@ -59,6 +64,8 @@ struct pc2_batch {
   int win_dec[pc2::kBatchClasses] = {};
   std::vector<pc2::BatchNode> nodes;
   std::vector<size_t> dct_off;                  // per node: word offset of its decrypted plaintexts (per-node path)
+  std::vector<char> tc_node;                    // per node: runs on the tensor-core engine, not in the work list
+  int tc_nodes = 0;
   double kappa = 0, zmin = 0, scale = 0, qmax = 0, inv_s2 = 0;
   long long mS = 0, S = 0;
   uint64_t seed = 0;
@@ -200,7 +207,10 @@ static int reset_state(pc2_batch* B, cudaStream_t st) {
   return PC2_OK;
 }
 
-static int per_node_round(pc2_batch* B, cudaStream_t st) {
+// One round node by node through the per-operation entry points; with
+// tc_only the tensor-core nodes alone, leaving the round counter to the
+// persistent launch that follows.
+static int per_node_round(pc2_batch* B, cudaStream_t st, bool tc_only = false) {
   pc2_ctx* ctx = B->ctx;
   if (!B->zq.p) {
     PC2_TRYB(B->zq.alloc(B->N));
@@ -210,7 +220,11 @@ static int per_node_round(pc2_batch* B, cudaStream_t st) {
     PC2_TRYB(B->D.alloc(B->d_words));
   }
   uint32_t* round_ptr = reinterpret_cast<uint32_t*>(B->ctl.p) + 2;  // BatchCtl::round
-  for (int k = 0; k < B->K; ++k) {
+  int last = B->K - 1;
+  if (tc_only)
+    while (last >= 0 && !B->tc_node[last]) --last;
+  for (int k = 0; k <= last; ++k) {
+    if (tc_only && !B->tc_node[k]) continue;
     const BatchNode& nd = B->nodes[k];
     const pc2_key* key = B->key[nd.cls];
     const size_t o = nd.elem0, n = nd.count;
@@ -232,7 +246,7 @@ static int per_node_round(pc2_batch* B, cudaStream_t st) {
     PC2_TRYB(decrypt_at(ctx, key, xh, n, Dk, st, 0));
     PC2_TRYB(launch_batch_update(Dk, key->Lh, n, B->zq.p + o, B->vq.p + o, B->b.p + o, B->mS, B->S, B->inv_s2,
                                  B->kappa, B->x.p + o, B->z.p + o, B->v.p + o, ctx->status,
-                                 k == B->K - 1 ? round_ptr : nullptr, ctx->sms, st));
+                                 !tc_only && k == last ? round_ptr : nullptr, ctx->sms, st));
   }
   return PC2_OK;
 }
@@ -295,8 +309,11 @@ int pc2_batch_create(pc2_ctx* ctx, const pc2_batch_params* prm, const double* d_
     e0 += (size_t)nk;
     ct += pc2_tiled_words((size_t)nk, 2 * Lh);
     dw += pc2_tiled_words((size_t)nk, Lh);
+    const bool tc = Lh == 64 && (ctx->engine == PC2_ENGINE_TC || (ctx->engine < 0 && nk >= PC2_TC_MIN_COUNT));
+    B->tc_node.push_back(tc ? 1 : 0);
+    B->tc_nodes += tc ? 1 : 0;
     const uint32_t G = (uint32_t)(kThreads / batch_lanes(Lh));
-    for (uint32_t f = 0; f < (uint32_t)nk; f += G)
+    for (uint32_t f = 0; !tc && f < (uint32_t)nk; f += G)
       B->items.push_back(BatchItem{(uint32_t)k, f, std::min(G, (uint32_t)nk - f), (uint32_t)c});
   }
   B->N = e0;
@@ -312,8 +329,8 @@ int pc2_batch_create(pc2_ctx* ctx, const pc2_batch_params* prm, const double* d_
     return PC2_ENOMEM;
   if (cudaMemcpyAsync(B->d_nodes.p, B->nodes.data(), B->nodes.size() * sizeof(BatchNode), cudaMemcpyHostToDevice,
                       st) ||
-      cudaMemcpyAsync(B->d_items.p, B->items.data(), B->items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                      st))
+      (!B->items.empty() && cudaMemcpyAsync(B->d_items.p, B->items.data(), B->items.size() * sizeof(BatchItem),
+                                            cudaMemcpyHostToDevice, st)))
     return PC2_ECUDA;
   // b = Gamma2(Bbar_ii); alpha-hat = E(Gamma1(alpha)) per node with the node's key (r-stream 0)
   DBuf<uint64_t> c1;
@@ -368,8 +385,10 @@ int pc2_batch_round(pc2_batch* B, int rounds, pc2_stream_t stream) {
       return PC2_ECUDA;
     }
   }
-  for (int r = 0; r < rounds; ++r)
+  for (int r = 0; r < rounds; ++r) {
+    if (B->tc_nodes) PC2_TRYB(per_node_round(B, st, true));
     if (cudaGraphLaunch(B->graph, st) != cudaSuccess) return PC2_ECUDA;
+  }
   return PC2_OK;
 }
 
@@ -433,6 +452,13 @@ int pc2_batch_tune(pc2_batch* B, int sample_items, pc2_stream_t stream, int* h_r
         sample.push_back(it);
         ++counts[it.cls];
       }
+  }
+  if (sample.empty()) {  // every node on the tensor-core engine: nothing to tune
+    if (h_result) {
+      for (int c = 0; c < kBatchClasses; ++c) h_result[c] = B->key[c] ? B->win_enc[c] : 0;
+      h_result[kBatchClasses] = B->blocks_per_sm;
+    }
+    return PC2_OK;
   }
   DBuf<BatchItem> d_sample;
   PC2_TRYB(d_sample.alloc(sample.size()));

@@ -1,6 +1,7 @@
 // batch_kernels.cu -- the batched private ADMM round: one persistent launch
-// runs the whole round of every element of every edge node, whatever the
-// node's key size (pc2_batch.h states the element-wise form of the round).
+// runs the whole round of every element of every edge node in its work list,
+// whatever the node's key size (pc2_batch.h states the element-wise form of
+// the round; the host leaves out the nodes it runs on the tensor cores).
 //
 //   k_batch_round   persistent CTAs claim work items (up to 128 / lanes
 //                   consecutive elements of one node) from a cost-ordered

@@ -271,6 +271,22 @@ static int enc_crt_round(pc2_ctx* ctx, const pc2_key* key, const uint64_t* m64, 
   P->split = split;
   P->kind2 = kind2;
   P->base2 = base2;
+  if constexpr (Lh == 64) {
+    // the tensor-core engine per vector (elements [0, split) with stream
+    // kind, the rest with kind2 at counter e0 + (e - split), output base2)
+    const size_t n1 = split < count ? split : count, n2 = count - n1;
+    if (use_tc(ctx, n1 > n2 ? n1 : n2)) {
+      auto K = tc_mods(key, &rc);
+      if (!K) return rc;
+      rc = n1 ? launch_enc_crt_tc(*P, *K, m64, nullptr, n1, out, ctx_scratch, ctx, ctx->status, ctx->sms, st, base,
+                                  nullptr)
+              : PC2_OK;
+      if (rc != PC2_OK || !n2) return rc;
+      P->kind = kind2;
+      return launch_enc_crt_tc(*P, *K, m64 + n1, nullptr, n2, out, ctx_scratch, ctx, ctx->status, ctx->sms, st,
+                               base2, nullptr);
+    }
+  }
   return with_crt_lanes<Lh>(cfg.T, [&](auto tt) {
     constexpr int T = decltype(tt)::value;
     if (cfg.split)  // both vectors in one launch

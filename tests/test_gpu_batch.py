@@ -152,3 +152,68 @@ def test_one_key_size_and_single_node(env):
     assert np.array_equal(x.cpu().numpy(), ref.x[1]) and np.array_equal(v.cpu().numpy(), ref.v[1])
     assert bt.info()["items"] == 3
     bt.close()
+
+
+def _check_round_cts(env, bt, keys, sizes, node_key, ref, T, nodes, picks):
+    """Ciphertexts of round T on the picked elements of the given nodes against the oracle."""
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    zq, vq = O.gamma2(ref.z[T - 2], QP), O.gamma2(-ref.v[T - 2], QP)
+    for k in nodes:
+        n = sizes[k]
+        kg, ko = keys[node_key[k]]
+        zh, vh, xh = _cts(env, bt, "zhat", k, n), _cts(env, bt, "vhat", k, n), _cts(env, bt, "xhat", k, n)
+        for i in picks(n):
+            e = int(offs[k] + i)
+            assert zh[i] == P.encrypt(ko, [int(zq[e])], [P.r_of(ko, SEED, O.stream_id(T, O.KIND_Z), e)])[0], (k, i)
+            assert vh[i] == P.encrypt(ko, [int(vq[e])], [P.r_of(ko, SEED, O.stream_id(T, O.KIND_V), e)])[0], (k, i)
+            assert P.decrypt(ko, [xh[i]])[0] == ref.D[T - 1][e], (k, i)
+
+
+def test_forced_tensor_core_nodes_match_oracle(env):
+    """With the engine forced to the tensor cores every 2048-bit node leaves the
+    work list and runs node by node before the persistent launch of each round;
+    iterates and ciphertexts stay those of the oracle."""
+    torch, pc2, ctx = env
+    pc2.set_engine(ctx, pc2.ENGINE_TC)
+    try:
+        st, keys, bt = _make(env, SIZES, NODE_KEY, BITS)
+        G = {256: 128, 512: 128, 1024: 128, 2048: 128, 3072: 32}
+        assert bt.info()["items"] == sum(-(-n // G[BITS[k]]) for n, k in zip(SIZES, NODE_KEY) if BITS[k] != 2048)
+        T = 3
+        ref = O.quantized_admm(st, 0.02, 1.0, T, QP)
+        for t in range(1, T + 1):
+            bt.round(1)
+            x, z, v, nxt = bt.get()
+            assert nxt == t + 1
+            assert np.array_equal(x.cpu().numpy(), ref.x[t - 1]) and np.array_equal(v.cpu().numpy(), ref.v[t - 1])
+        assert ctx.status() == 0
+        nodes = [k for k in range(len(SIZES)) if BITS[NODE_KEY[k]] == 2048] + [0, 4]
+        _check_round_cts(env, bt, keys, SIZES, NODE_KEY, ref, T, nodes, lambda n: sorted({0, n // 2, n - 1}))
+        bt.close()
+    finally:
+        pc2.set_engine(ctx, -1)
+
+
+def test_large_2048_node_on_tensor_cores_automatic(env):
+    """A 2048-bit node of PC2_TC_MIN_COUNT + 16 elements (tensor-core engine, a
+    ragged last tile) beside a small 1024-bit node (the persistent launch):
+    iterates equal the oracle's and the per-node path's; sampled ciphertexts
+    of both nodes equal the oracle's."""
+    torch, pc2, ctx = env
+    sizes, node_key = [16384 + 16, 50], [0, 1]
+    st, keys, bt = _make(env, sizes, node_key, [2048, 1024])
+    assert bt.info()["items"] == 1
+    T = 2
+    ref = O.quantized_admm(st, 0.02, 1.0, T, QP)
+    bt.round(T)
+    x, z, v, nxt = bt.get()
+    assert nxt == T + 1 and ctx.status() == 0
+    assert np.array_equal(x.cpu().numpy(), ref.x[T - 1]) and np.array_equal(z.cpu().numpy(), ref.z[T - 1])
+    assert np.array_equal(v.cpu().numpy(), ref.v[T - 1])
+    _check_round_cts(env, bt, keys, sizes, node_key, ref, T, [0, 1], lambda n: sorted(i for i in {0, 127, 128, n // 2, n - 1} if i < n))
+    _, _, b2 = _make(env, sizes, node_key, [2048, 1024])
+    b2.round_per_node(T)
+    g = b2.get()
+    assert torch.equal(g[0], x) and torch.equal(g[1], z) and torch.equal(g[2], v) and g[3] == T + 1
+    b2.close()
+    bt.close()
