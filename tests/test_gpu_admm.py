@@ -209,6 +209,32 @@ def test_matvec_forms_bit_identical(env, nbits):
 
 
 @pytest.mark.parametrize("per_node", [False, True])
+def test_tensor_core_engine_rounds_bit_exact(env, per_node):
+    """2048-bit n with the engine forced to the tensor cores: the rounds'
+    encryptions (z-hat and (-v)-hat in one call, r-streams from the device
+    round counter) and decryptions take the tensor-core kernels, inside the
+    captured round graph from round 2 on; iterates equal the oracle's."""
+    torch, pc2, ctx = env
+    L = W.lasso_small(seed=7, M=24, N=60, nnz=4, K=2)
+    pc2.set_engine(ctx, pc2.ENGINE_TC)
+    try:
+        st, kg, ko, adm = _make(env, L, 2048, seed=23, per_node=per_node)
+        ref = O.quantized_admm(st, L.lam, L.rho, 3, QP)
+        for t in range(3):
+            adm.round(1)
+            x, z, v, nxt = adm.get()
+            assert nxt == t + 2
+            assert np.array_equal(x.cpu().numpy(), ref.x[t]) and np.array_equal(v.cpu().numpy(), ref.v[t]), t
+        b = adm.buffers()
+        D = pc2.tiled_to_ints(ctx, _ints(pc2, b["D"], 60, kg.limbs), 60, kg.limbs)
+        assert D == ref.D[2]
+        assert ctx.status() == 0
+        adm.close()
+    finally:
+        pc2.set_engine(ctx, -1)
+
+
+@pytest.mark.parametrize("per_node", [False, True])
 def test_missing_edge_node_refuses_round_then_resumes(env, per_node):
     """Failure detection: while an edge node's segment is marked missing the
     round is refused (PC2_EMISSING) with x, z, v and the round counter
